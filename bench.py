@@ -1,0 +1,331 @@
+"""Benchmark: KSG CMI estimates per second (surrogates included) at T = 10000.
+
+Workload (default "var10"): full greedy multivariate TE network inference on a
+seeded 10-node linear VAR (directed ER graph p = 0.3, self coupling 0.5,
+couplings U(0.1, 0.5) at random lags 1-5, spectral radius 0.9, sigma = 1),
+T = 10000 float32 samples, max lag 5, KSG k = 4, 200 surrogates per test,
+alpha = 0.05.  One step = te_network_infer over every target (all rows of
+the hot path: embeddings, permutations, fused kNN + counts + digamma keys,
+test statistics, greedy control, network assembly).
+
+value : estimates / s with the series already resident on the device.
+e2e   : the same through the C ABI from a host buffer: each step uploads the
+        series (te_data_create from host memory) and reads results back.
+Under torchrun each rank infers its own replica data set (seed + rank), no
+collective on the data path ("scaling": "weak").
+
+--impl reference times the CPU oracle (brute-force C, all host cores) on a
+bounded sample of the same workload: the members of step-2 groups.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "KSG CMI estimates/s incl. surrogates at T=10000"
+UNIT = "estimates/s"
+SM_COUNT = 152
+OPS_PER_MEMBER_PAIR = 10  # kNN pass: sub, max, compare; count pass: sub, 3 compares, 3 adds
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _workload(name, T, seed):
+    import synth
+    if name == "var10":
+        w = synth.workload_var10(T=T, seed=seed)
+        params = dict(k=4, max_lag_target=5, max_lag_sources=5, n_surr=200, alpha_max=0.05,
+                      alpha_min=0.05, alpha_omnibus=0.05, seed=seed)
+        desc = (f"var10: 10-node VAR, ER p=0.3, T={T}, max lag 5, k=4, S=200, alpha=0.05, "
+                "full greedy inference over all targets")
+    elif name == "clm100":
+        w = synth.workload_clm100(T=T, seed=seed)
+        params = dict(k=4, max_lag_target=5, max_lag_sources=5, n_surr=200, alpha_max=0.05,
+                      alpha_min=0.05, alpha_omnibus=0.05, seed=seed)
+        desc = f"clm100: 100-node coupled logistic maps, T={T}, max lag 5, k=4, S=200"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return w["series"], params, desc
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_sample(series, params, budget_s=20.0, members=None):
+    """Time the oracle on members of the first step-2 group of target 0
+    (Y = target present, Z = its lag-1 past, X = each source candidate,
+    identity plus surrogates), all host cores."""
+    from oracle import ksg as oksg
+    n_proc, T = series.shape
+    t0 = max(params["max_lag_target"], params["max_lag_sources"])
+    N = T - t0
+    cands = [(q, l) for q in range(1, n_proc) for l in range(1, params["max_lag_sources"] + 1)]
+    S = 7
+    perms = np.stack([oksg.permutation(params["seed"], 0, 2, 0, s, N) for s in range(1, S + 1)])
+    threads = oksg.max_threads()
+    # calibrate with one member per thread, then size the sample to the budget
+    def run(nm):
+        xs, pidx = [], []
+        for a in range(nm):
+            xs.append([cands[a % len(cands)]])
+            pidx.append((a % (S + 1)) - 1)
+        t = time.perf_counter()
+        oksg.cmi_ksg_batch(series, xs, [(0, 0)], [(0, 1)], perms=perms, perm_idx=pidx,
+                           k=params["k"], max_lag=t0, n_threads=threads)
+        return time.perf_counter() - t
+    if members is None:
+        dt = run(threads)
+        per = dt / threads
+        members = max(threads, int(budget_s / max(per, 1e-6)) // threads * threads)
+        members = min(members, 40 * threads)
+    dt = run(members)
+    return {"value": members / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": (f"{members} members (step-2 group of target 0: source candidates x "
+                       f"identity/7 surrogates, Z = target lag 1) at N={N}, brute-force C "
+                       f"oracle, {threads} OpenMP threads, {dt:.1f} s")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    series, params, desc = _workload(args.workload, args.T, 1)
+    from oracle import ksg as oksg
+    threads = oksg.max_threads()
+    # size one step to ~20 s of CPU work
+    calib = cpu_oracle_sample(series, params, members=threads)
+    per_member = calib["cores"] / calib["value"]
+    members = max(threads, int(20.0 / per_member) // threads * threads)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(series, params, members=threads)
+    vals = []
+    t_all = 0.0
+    n_all = 0
+    for _ in range(args.steps):
+        r = cpu_oracle_sample(series, params, members=members)
+        vals.append(r)
+        t_all += members / r["value"]
+        n_all += members
+    value = n_all / t_all
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": desc, "sample": vals[-1]["sample"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": vals[-1]["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="var10")
+    ap.add_argument("--T", type=int, default=10000)
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--targets", default="all", help="comma list of targets, or 'all'")
+    args = ap.parse_args()
+
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import paper_1902_06828_gb300 as te
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    series, params, desc = _workload(args.workload, args.T, 1 + rank)
+    if args.targets != "all":
+        params["targets"] = [int(v) for v in args.targets.split(",")]
+        desc += f", targets {args.targets}"
+
+    ctx = te.Context(local)
+    stream = torch.cuda.current_stream()
+    ctx.set_stream(stream)
+    data = te.te_data_create(ctx, series)
+    flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(d):
+        return te.te_network_infer(ctx, d, **params)
+
+    for _ in range(args.warmup):
+        step(data)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    s0 = ctx.stats()
+    n_est = 0
+    barrier()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        if flush is not None:
+            flush.fill_(1)
+        r = step(data)
+        n_est += r["n_estimates"]
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    s1 = ctx.stats()
+    ms = ev0.elapsed_time(ev1)
+
+    # end to end through the C ABI with host buffers
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else args.steps
+    host = torch.from_numpy(series).pin_memory()
+    e_est = 0
+    sb = ctx.stats()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        if flush is not None:
+            flush.fill_(1)
+        d = te.te_data_create(ctx, host)
+        r = step(d)
+        e_est += r["n_estimates"]
+        d.close()
+    e1.record(stream)
+    barrier()
+    se = ctx.stats()
+    e_ms = e0.elapsed_time(e1)
+
+    t = torch.tensor([ms, e_ms, float(n_est), float(e_est)], dtype=torch.float64, device="cuda")
+    if dist:
+        mx = t[:2].clone()
+        sm = t[2:].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms, e_ms = mx.tolist()
+        n_est, e_est = sm.tolist()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    kernel_ms = s1["kernel_ms"] - s0["kernel_ms"]
+    pair_evals = s1["pair_evals"] - s0["pair_evals"]
+    ksg_launches = s1["ksg_launches"] - s0["ksg_launches"]
+    ops = OPS_PER_MEMBER_PAIR * pair_evals / 2.0
+    achieved = ops / (kernel_ms / 1e3) / 1e12 if kernel_ms > 0 else None
+    peak = SM_COUNT * 128 * sm_max * 1e6 / 1e12
+    value = n_est / (ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "estimates_per_step": n_est / args.steps / world,
+                   "l2": "flushed before every step (256 MB write)" if flush is not None
+                   else "not flushed", "parallelism": f"replicas{world}"},
+        "e2e": {"value": e_est / (e_ms / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": (se["h2d_bytes"] - sb["h2d_bytes"]) / max(e2e_steps, 1),
+                "d2h_bytes_per_step": (se["d2h_bytes"] - sb["d2h_bytes"]) / max(e2e_steps, 1),
+                "steps": e2e_steps},
+        "gpu_launches": s1["launches"] - s0["launches"],
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": "ksg_fused_kernel", "kernel_ms_per_launch":
+                     kernel_ms / max(ksg_launches, 1), "launches": ksg_launches,
+                     "peak_note": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived)"},
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_oracle_sample(series, params)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,242 @@
+/*
+ * te_ksg.h -- C ABI of the GB300 (sm_103a) KSG conditional-mutual-information
+ * engine and greedy multivariate transfer-entropy network inference.
+ *
+ * Method: Novelli, Wollstadt, Mediano, Wibral & Lizier, "Large-scale directed
+ * network inference with multivariate transfer entropy and hierarchical
+ * statistical testing" (Network Neuroscience 2019, arXiv:1902.06828).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * - Every function returns te_status.  On any error the output buffers are left
+ *   untouched and te_last_error(ctx) holds a one-line reason until the next call
+ *   on that context.  No C++ exception crosses this boundary.
+ * - The caller owns every pointer it passes in (inputs and output buffers).
+ *   The library owns te_ctx, te_data and te_network_result objects and frees
+ *   them through te_ctx_destroy, te_data_destroy and te_network_result_free.
+ * - A context is used by one host thread at a time; different contexts are
+ *   independent.  All device work of a context runs on its stream (its own
+ *   stream by default, or one set with te_ctx_set_stream); blocking calls
+ *   synchronise that stream before they return.
+ * - Variables are (process, lag) pairs (Methods, "Definitions and assumptions":
+ *   the target present Y_t, candidate target past Y_{t-1..t-l_target}, candidate
+ *   sources past X_{i,t-1..t-l_sources}).  For an estimate with maximum lag L,
+ *   point i (i = 0..N-1, N = T - L) sits at time t_i = L + i, and variable
+ *   (p, lag) takes the value series[p][t_i - lag] there.  Lag 0 is the present.
+ * - Time series are float32, row-major [n_proc][T], finite values only.
+ */
+#ifndef TE_KSG_H
+#define TE_KSG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TE_OK = 0,
+    TE_EINVAL = -1,      /* an argument breaks a documented rule */
+    TE_ENOMEM = -2,      /* host or device allocation failed */
+    TE_ECUDA = -3,       /* a CUDA runtime call failed (the message names it) */
+    TE_ETIMEOUT = -4,    /* te_serve_poll: the job did not finish in time */
+    TE_ECANCELLED = -5,  /* te_serve_poll: the job was cancelled */
+    TE_EBUSY = -6,       /* te_serve_submit: the job can never fit the device budget */
+    TE_EINTERNAL = -7    /* a bug: please report the message */
+} te_status;
+
+typedef struct te_ctx te_ctx;
+typedef struct te_data te_data;
+
+typedef struct {
+    int32_t proc; /* process index, 0 <= proc < n_proc */
+    int32_t lag;  /* 0 = present, 1.. = past samples; lag <= the estimate's max lag */
+} te_var;
+
+/* Limits of this build. */
+#define TE_MAX_DIMS 32      /* dx + dy + dz of one estimate */
+#define TE_MAX_K 16         /* nearest neighbours */
+
+/* ---- context and data ---------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  It owns a stream, a grow-only
+ * device workspace and the digamma fixed-point table (see cmi_ksg).
+ * Errors: TE_EINVAL (out NULL or bad device), TE_ECUDA, TE_ENOMEM. */
+te_status te_ctx_create(int device, te_ctx **out);
+
+/* Run all later work of ctx on `cuda_stream` (a cudaStream_t of the same device,
+ * e.g. torch.cuda.current_stream().cuda_stream); NULL restores the context's
+ * own stream.  The caller keeps ownership of the stream. */
+te_status te_ctx_set_stream(te_ctx *ctx, void *cuda_stream);
+
+void te_ctx_destroy(te_ctx *ctx);
+
+/* One-line reason for the last failed call on ctx ("" after success).  The
+ * string stays valid until the next call on ctx.  NULL ctx -> static text. */
+const char *te_last_error(const te_ctx *ctx);
+
+/* Copy float32 [n_proc][T] series (host memory when series_on_device == 0,
+ * else a device pointer of the context's device) into a device-resident data
+ * set owned by the library.  The caller keeps ownership of `series`.
+ * Errors: TE_EINVAL (NULL pointers, n_proc < 1, T < 2, a non-finite value),
+ * TE_ENOMEM, TE_ECUDA. */
+te_status te_data_create(te_ctx *ctx, const float *series, int32_t n_proc, int32_t T,
+                         int series_on_device, te_data **out);
+void te_data_destroy(te_data *data);
+
+/* ---- one KSG estimate and its surrogates ---------------------------------- */
+
+typedef struct {
+    int32_t k;           /* nearest neighbours, 1..TE_MAX_K (paper: 4) */
+    int32_t theiler;     /* Theiler window w >= 0: pairs with |i - j| <= w are
+                            excluded from every search (0 = only j == i) */
+    int32_t max_lag;     /* L: first point at time L, N = T - L points; every
+                            variable's lag must be <= L */
+    int32_t n_surr;      /* S >= 0 permutation surrogates of X */
+    uint64_t seed;       /* surrogate generator seed */
+    uint64_t stream_tag; /* selects an independent surrogate stream */
+} te_ksg_params;
+
+/*
+ * KSG estimate of the conditional mutual information I(X; Y | Z) and of its
+ * S permutation surrogates I(X o pi_s; Y | Z).
+ *
+ * Estimator (Methods, "Coupled logistic maps process": Kraskov's I^(1) with
+ * k nearest neighbours and its extension to CMI; Statistical tests, "Maximum
+ * statistic test": surrogates shuffle the embedded source samples, the
+ * target is never shuffled):
+ *   max-norm distances in float32, d_V(i,j) = max over V's variables of
+ *   |v_i - v_j| (the subtraction is the only rounding; d_Z = -inf if dz = 0);
+ *   eps_i = k-th smallest max(d_X, d_Y, d_Z) over valid j (j != i, |i-j| > w);
+ *   n_xz, n_yz, n_z = numbers of valid j with max(d_X,d_Z), max(d_Y,d_Z), d_Z
+ *   strictly below eps_i;
+ *   I = psi(k) + (1/N) sum_i [psi(n_z+1) - psi(n_xz+1) - psi(n_yz+1)].
+ * The sum is accumulated exactly as the 128-bit integer
+ *   K = sum_i (Q[n_z+1] - Q[n_xz+1] - Q[n_yz+1]),  Q[n] = round(2^52 psi(n)),
+ * and reported as I = Q[k] 2^-52 + (double)K / (2^52 N), so results do not
+ * depend on summation order and every decision is exact.
+ *
+ * Surrogate s (1..S) reads X at point i from point pi_s(i), pi_s a Fisher-Yates
+ * permutation of [0, N) driven by SplitMix64 keyed by (seed, stream_tag, stage
+ * 0, iteration 0, s).  Y and Z are never permuted.
+ *
+ * x, y, z: host arrays of dx >= 1, dy >= 1, dz >= 0 variables (z may be NULL
+ * when dz == 0); dx + dy + dz <= TE_MAX_DIMS.
+ * out_cmi: host double[1 + S]; [0] is the original estimate, [s] surrogate s.
+ * out_key: host int64[2 (1 + S)] or NULL; pairs (hi, lo) of K in two's
+ * complement (lo holds the low 64 bits as an unsigned value).
+ * Errors: TE_EINVAL (NULL pointers, a variable outside the data, lag > max_lag,
+ * max_lag >= T, k outside 1..TE_MAX_K, fewer than k valid neighbours for some
+ * point, too many dims, n_surr < 0), TE_ENOMEM, TE_ECUDA.
+ */
+te_status cmi_ksg(te_ctx *ctx, const te_data *data, const te_var *x, int32_t dx,
+                  const te_var *y, int32_t dy, const te_var *z, int32_t dz,
+                  const te_ksg_params *params, double *out_cmi, int64_t *out_key);
+
+/* Parity/debug form of cmi_ksg for one member (0 = original, s = surrogate s):
+ * per-point eps (float[N]) and counts n_xz, n_yz, n_z (int32[N] each) in
+ * host memory; any of the four may be NULL.  Same errors as cmi_ksg, plus
+ * TE_EINVAL when member is outside 0..n_surr. */
+te_status cmi_ksg_debug(te_ctx *ctx, const te_data *data, const te_var *x, int32_t dx,
+                        const te_var *y, int32_t dy, const te_var *z, int32_t dz,
+                        const te_ksg_params *params, int32_t member, float *eps,
+                        int32_t *n_xz, int32_t *n_yz, int32_t *n_z);
+
+/* A batch job: one cmi_ksg call (the original plus params.n_surr surrogates). */
+typedef struct {
+    const te_data *data;
+    const te_var *x, *y, *z;
+    int32_t dx, dy, dz;
+    te_ksg_params params;
+} te_cmi_job;
+
+/* Evaluate many jobs in fused launches.  Results are identical to calling
+ * cmi_ksg once per job.  out: host double[sum_j (1 + S_j)], jobs in order.
+ * out_key: NULL or host int64[2 sum_j (1 + S_j)].  Errors as cmi_ksg (the
+ * message names the offending job). */
+te_status cmi_ksg_batch(te_ctx *ctx, const te_cmi_job *jobs, int32_t n_jobs, double *out,
+                        int64_t *out_key);
+
+/* ---- greedy network inference -------------------------------------------- */
+
+typedef struct {
+    int32_t k, theiler;            /* estimator parameters, as te_ksg_params */
+    int32_t max_lag_target;        /* l_target >= 1 */
+    int32_t max_lag_sources;       /* l_sources >= 1 */
+    int32_t n_surr;                /* S; every test needs S * alpha > 1 */
+    double alpha_max, alpha_min, alpha_omnibus, alpha_seq;
+    int32_t seq_test;              /* 1: run the step-down stage after the omnibus test */
+    int32_t fdr;                   /* 1: Benjamini-Hochberg over targets' omnibus p-values */
+    double alpha_fdr;
+    uint64_t seed;
+    const int32_t *targets;        /* host array of target processes, or NULL = all */
+    int32_t n_targets;
+} te_infer_params;
+
+typedef struct {
+    int32_t target;
+    int32_t n_sel_target;
+    te_var *sel_target;            /* selected target past, (proc, lag) ascending */
+    int32_t n_sel_sources;
+    te_var *sel_sources;           /* selected sources past, ascending */
+    double omnibus_cmi, omnibus_p; /* collective TE of the selected sources and its p */
+    int32_t omnibus_tested;        /* 1 if the omnibus test ran */
+    int32_t significant;           /* 1 if the target keeps sources */
+    uint64_t n_estimates;          /* CMI estimates (surrogates included) for this target */
+} te_target_result;
+
+typedef struct {
+    int32_t n_proc, n_targets;
+    te_target_result *targets;
+    uint8_t *adjacency;            /* [n_proc * n_proc], adjacency[src * n_proc + tgt] */
+    int32_t *min_lag;              /* [n_proc * n_proc], smallest selected lag, 0 = no link */
+    uint64_t n_estimates;          /* total CMI estimates */
+    double seconds;                /* wall time of the inference */
+} te_network_result;
+
+/*
+ * Greedy multivariate TE network inference with hierarchical tests (Methods,
+ * "Inference algorithm" steps 1-4 and "Statistical tests"), every CMI by the
+ * KSG estimator above, every test by S permutation surrogates:
+ *   step 1 selects the target past by repeated maximum-statistic tests,
+ *   step 2 selects the sources past conditioned on what was selected,
+ *   step 3 prunes the sources past with minimum-statistic tests,
+ *   step 4 runs the omnibus test on the collective TE;
+ *   optional: a step-down test after the omnibus (seq_test) and FDR across
+ *   targets (fdr).  A link src -> tgt exists when a variable of src is in the
+ *   target's selected sources past.
+ * Readings where the paper is silent (all documented with the library):
+ * p = #{surrogate statistic > observed} / S, significant iff p < alpha; ties in
+ * argmax / argmin go to the first candidate in canonical (proc, lag) order;
+ * one permutation per (target, stage, iteration, surrogate) is shared by all
+ * candidates of a test; pruning stops at the first significant minimum; a
+ * failed omnibus test empties the target's sources.
+ * All targets use the same N = T - max(l_target, l_sources) points.
+ * Result: library-owned, free with te_network_result_free.
+ * Errors: TE_EINVAL (bad parameters, S * alpha <= 1, targets out of range,
+ * too few points), TE_ENOMEM, TE_ECUDA.
+ */
+te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_params *params,
+                           te_network_result **out);
+void te_network_result_free(te_network_result *res);
+
+/* Counters of a context since its creation. */
+typedef struct {
+    uint64_t estimates;       /* CMI estimates (members) evaluated */
+    uint64_t launches;        /* kernel launches issued (all kernels of the library) */
+    uint64_t pair_evals;      /* member x point-pair distance evaluations (both passes) */
+    double kernel_ms;         /* summed device time of the KSG kernels (CUDA events on the
+                                 context's stream) */
+    uint64_t ksg_launches;    /* launches of the fused KSG kernel */
+    uint64_t h2d_bytes;       /* bytes copied host -> device by the library */
+    uint64_t d2h_bytes;       /* bytes copied device -> host by the library */
+} te_stats;
+
+te_status te_get_stats(const te_ctx *ctx, te_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TE_KSG_H */

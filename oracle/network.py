@@ -235,6 +235,7 @@ def infer_target(series, target: int, p: Params) -> TargetResult:
 
     res.sel_target = sorted(sel_y)
     res.sel_sources = sorted(sel_x)
+    res.significant = res.significant and bool(sel_x)
     return res
 
 

@@ -1,0 +1,87 @@
+// Internal interface between the host runtime and the sm_103a kernels.
+// Not part of the public ABI (include/te_ksg.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace teksg {
+
+// A group is a set of members (CMI estimates) that share the conditioning
+// variables Z, the target variables Y, the point set and k.  Members differ in
+// their X variables and in the permutation applied to X.
+struct GroupDesc {
+    const float *base;      // device series of the group's data set
+    int N;                  // points
+    int k;                  // neighbours
+    int theiler;            // Theiler window
+    int dy, dz, dx;         // dims
+    int ycol, zcol;         // first index into cols[] of the Y / Z column offsets
+    int member_begin;       // first member of the group in members[]
+    int n_members;
+    int n_qtiles;           // ceil(N / query tile)
+    int n_mblocks;          // ceil(n_members / members per thread)
+    long long item_begin;   // first CTA of the group in the launch
+};
+
+struct MemberDesc {
+    const int32_t *perm;    // device permutation of [0, N) applied to X, or nullptr
+    int xcol;               // first index into cols[] of the dx X column offsets
+    int out;                // output slot
+};
+
+// A column is addressed as base + off: the value of the column at point i is
+// base[off + i], off = proc * T + max_lag - lag.
+struct KsgLaunch {
+    const GroupDesc *groups;
+    int n_groups;
+    const MemberDesc *members;
+    const int *cols;
+    const int64_t *q;              // digamma fixed-point table Q[0..q_len)
+    unsigned long long *acc;       // [2 * n_out]: (low-32-bit partial sums, high parts)
+    float *dbg_eps;                // per-point debug outputs for member slot dbg_out
+    int *dbg_nxz, *dbg_nyz, *dbg_nz;
+    int dbg_out;
+    int jt;                        // points per staged j tile
+};
+
+// Kernel variants: members per thread and k.  kgen = 0 means k is a template
+// constant; otherwise a runtime k <= TE_MAX_K.
+struct KsgVariant {
+    int m;      // members per thread
+    int kt;     // template k (0 = runtime k)
+    int qt;     // query points per CTA (threads)
+};
+
+cudaError_t launch_ksg(const KsgLaunch &L, const KsgVariant &v, long long n_items, bool dx1,
+                       size_t smem_bytes, cudaStream_t st);
+size_t ksg_smem_bytes(const KsgVariant &v, int dy, int dz, int dx, bool dx1, int jt);
+cudaError_t ksg_prepare_attributes();
+
+// Fisher-Yates permutations of [0, n), one per surrogate s = s_first .. s_first +
+// n_perm - 1, keyed by SplitMix64 over (seed, target, stage, iter, s).
+cudaError_t launch_perms(int32_t *out, long long stride, int n, uint64_t seed, uint64_t target,
+                         uint64_t stage, uint64_t iter, int s_first, int n_perm, cudaStream_t st);
+
+// acc (low, high partial sums) -> normalised 128-bit keys (hi, lo) per slot.
+cudaError_t launch_finalize(const unsigned long long *acc, long long *keys, int n_out,
+                            cudaStream_t st);
+
+// Test statistics over keys laid out [n_cand][S + 1] (slot c * (S + 1) + s
+// from req.slot): mode 0 = maximum statistic, 1 = minimum statistic.  One CTA
+// per request writes ibuf[cnt_off] = argmax (or argmin) of the originals (ties
+// -> lowest index), ibuf[cnt_off + 1 + c] = #{s : null_s > original_c} with
+// null_s the max (or min) over candidates of surrogate s, and the originals as
+// (hi, lo) pairs at obuf[2 (orig_off + c)].
+struct StatReq {
+    long long slot;
+    int n_cand, S, mode;
+    int cnt_off, orig_off;
+};
+cudaError_t launch_stats(const long long *keys, const StatReq *reqs, int n_req, int max_S,
+                         int *ibuf, long long *obuf, cudaStream_t st);
+
+// flag[0] = 1 if any of n values is not finite
+cudaError_t launch_check_finite(const float *x, long long n, int *flag, cudaStream_t st);
+
+}  // namespace teksg

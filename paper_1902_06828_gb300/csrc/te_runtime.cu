@@ -1,0 +1,737 @@
+// Host runtime of the KSG engine: contexts, data sets, the digamma table,
+// validation, the fused-launch engine and the cmi_ksg* entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "te_runtime.h"
+
+using namespace teksg;
+
+namespace teksg {
+
+te_status fail(te_ctx *ctx, te_status st, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+te_status cuda_fail(te_ctx *ctx, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + " failed: " + cudaGetErrorName(e) + " (" +
+                    cudaGetErrorString(e) + ")";
+    return fail(ctx, e == cudaErrorMemoryAllocation ? TE_ENOMEM : TE_ECUDA, m);
+}
+
+cudaError_t copy_h2d(te_ctx *ctx, void *dst, const void *src, size_t bytes)
+{
+    ctx->stats.h2d_bytes += bytes;
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream);
+}
+
+cudaError_t copy_d2h(te_ctx *ctx, void *dst, const void *src, size_t bytes)
+{
+    ctx->stats.d2h_bytes += bytes;
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+}
+
+te_status ensure_dev(te_ctx *ctx, DevBuf &b, size_t bytes)
+{
+    if (bytes <= b.cap) return TE_OK;
+    size_t want = std::max(bytes, b.cap + b.cap / 2);
+    want = (want + 255) & ~(size_t)255;
+    if (b.p) {
+        CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+        CK(cudaFree(b.p), "cudaFree");
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    CK(cudaMalloc(&b.p, want), "cudaMalloc");
+    b.cap = want;
+    return TE_OK;
+}
+
+te_status ensure_pin(te_ctx *ctx, size_t bytes)
+{
+    if (bytes <= ctx->pin_cap) return TE_OK;
+    size_t want = std::max(bytes, ctx->pin_cap + ctx->pin_cap / 2);
+    if (ctx->pin) {
+        CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+        CK(cudaFreeHost(ctx->pin), "cudaFreeHost");
+        ctx->pin = nullptr;
+        ctx->pin_cap = 0;
+    }
+    CK(cudaMallocHost(&ctx->pin, want), "cudaMallocHost");
+    ctx->pin_cap = want;
+    return TE_OK;
+}
+
+// ---- digamma fixed-point table, double-double arithmetic ----------------
+// psi(1) = -gamma and psi(n + 1) = psi(n) + 1/n, carried as an unevaluated sum
+// hi + lo of two doubles (error-free two-sum; 1/n split with an exact FMA
+// residual).  Q[n] = round-to-nearest(2^52 psi(n)).
+namespace {
+
+inline void two_sum(double a, double b, double &s, double &e)
+{
+    s = a + b;
+    const double bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+inline void quick_two_sum(double a, double b, double &s, double &e)
+{
+    s = a + b;
+    e = b - (s - a);
+}
+
+inline void dd_add(double ah, double al, double bh, double bl, double &rh, double &rl)
+{
+    double s, e, t, f;
+    two_sum(ah, bh, s, e);
+    two_sum(al, bl, t, f);
+    e += t;
+    quick_two_sum(s, e, s, e);
+    e += f;
+    quick_two_sum(s, e, rh, rl);
+}
+
+inline void dd_recip(double n, double &h, double &l)
+{
+    h = 1.0 / n;
+    const double r = std::fma(-h, n, 1.0);  // exact residual 1 - h n
+    l = r / n;
+}
+
+// divide a double-double by a small integer d
+inline void dd_div_int(double ah, double al, double d, double &rh, double &rl)
+{
+    const double q1 = ah / d;
+    const double r = std::fma(-q1, d, ah) + al;
+    const double q2 = r / d;
+    quick_two_sum(q1, q2, rh, rl);
+}
+
+void euler_gamma_dd(double &h, double &l)
+{
+    // decimal expansion of the Euler-Mascheroni constant, Horner from the end
+    static const char *digits = "5772156649015328606065120900824024310421593359399235988057672348848677";
+    double xh = 0.0, xl = 0.0;
+    for (int p = (int)std::strlen(digits) - 1; p >= 0; --p) {
+        double sh, sl;
+        dd_add((double)(digits[p] - '0'), 0.0, xh, xl, sh, sl);
+        dd_div_int(sh, sl, 10.0, xh, xl);
+    }
+    h = xh;
+    l = xl;
+}
+
+int64_t dd_to_q(double h, double l)
+{
+    const double hs = std::ldexp(h, 52), ls = std::ldexp(l, 52);
+    const double ip = std::floor(hs);
+    const double fp = hs - ip;  // exact
+    const double t = fp + ls;
+    return (int64_t)ip + (int64_t)std::floor(t + 0.5);
+}
+
+}  // namespace
+
+te_status ensure_q(te_ctx *ctx, int n_needed)
+{
+    if ((int)ctx->q_host.size() <= n_needed) {
+        if (ctx->q_host.empty()) {
+            ctx->q_host.push_back(0);  // psi has a pole at 0
+            double gh, gl;
+            euler_gamma_dd(gh, gl);
+            ctx->dd_hi = -gh;
+            ctx->dd_lo = -gl;
+            ctx->q_host.push_back(dd_to_q(ctx->dd_hi, ctx->dd_lo));  // n = 1
+        }
+        int target = std::max(n_needed + 1, (int)ctx->q_host.size() * 2);
+        target = std::max(target, 4096);
+        for (int n = (int)ctx->q_host.size(); n < target; ++n) {
+            double rh, rl;
+            dd_recip((double)(n - 1), rh, rl);
+            dd_add(ctx->dd_hi, ctx->dd_lo, rh, rl, ctx->dd_hi, ctx->dd_lo);
+            ctx->q_host.push_back(dd_to_q(ctx->dd_hi, ctx->dd_lo));
+        }
+    }
+    if (ctx->q_dev_len <= n_needed) {
+        if (ctx->q_dev) {
+            CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+            CK(cudaFree(ctx->q_dev), "cudaFree");
+            ctx->q_dev = nullptr;
+        }
+        const size_t bytes = ctx->q_host.size() * sizeof(int64_t);
+        CK(cudaMalloc(&ctx->q_dev, bytes), "cudaMalloc");
+        CK(copy_h2d(ctx, ctx->q_dev, ctx->q_host.data(), bytes), "cudaMemcpyAsync");
+        CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+        ctx->q_dev_len = (int)ctx->q_host.size();
+    }
+    return TE_OK;
+}
+
+double key_to_cmi(const te_ctx *ctx, int64_t hi, uint64_t lo, int k, int N)
+{
+    const __int128 K = ((__int128)hi << 64) | (__int128)lo;
+    const double psi_k = std::ldexp((double)ctx->q_host[k], -52);
+    const double t = (double)K;
+    const double d = 4503599627370496.0 * (double)N;
+    return psi_k + t / d;
+}
+
+te_status validate_estimate(te_ctx *ctx, const te_data *data, const te_var *x, int dx,
+                            const te_var *y, int dy, const te_var *z, int dz, int k, int theiler,
+                            int max_lag, int n_surr)
+{
+    if (!data) return fail(ctx, TE_EINVAL, "data is NULL");
+    if (data->ctx != ctx) return fail(ctx, TE_EINVAL, "data belongs to another context");
+    if (!x || dx < 1) return fail(ctx, TE_EINVAL, "x needs at least one variable");
+    if (!y || dy < 1) return fail(ctx, TE_EINVAL, "y needs at least one variable");
+    if (dz < 0 || (dz > 0 && !z)) return fail(ctx, TE_EINVAL, "z is NULL with dz > 0");
+    if (dx + dy + dz > TE_MAX_DIMS)
+        return fail(ctx, TE_EINVAL, "dx + dy + dz exceeds TE_MAX_DIMS (32)");
+    if (k < 1 || k > TE_MAX_K) return fail(ctx, TE_EINVAL, "k must be in 1..16");
+    if (theiler < 0) return fail(ctx, TE_EINVAL, "theiler window must be >= 0");
+    if (n_surr < 0) return fail(ctx, TE_EINVAL, "n_surr must be >= 0");
+    if (max_lag < 0 || max_lag >= data->T)
+        return fail(ctx, TE_EINVAL, "max_lag must be in 0..T-1");
+    const long long N = (long long)data->T - max_lag;
+    if (N - 1 - 2LL * theiler < k)
+        return fail(ctx, TE_EINVAL, "fewer than k valid neighbours for some point "
+                                    "(N - 1 - 2 theiler < k)");
+    const te_var *vs[3] = {x, y, z};
+    const int ds[3] = {dx, dy, dz};
+    for (int s = 0; s < 3; ++s)
+        for (int d = 0; d < ds[s]; ++d) {
+            const te_var v = vs[s][d];
+            if (v.proc < 0 || v.proc >= data->n_proc)
+                return fail(ctx, TE_EINVAL, "variable process outside the data");
+            if (v.lag < 0 || v.lag > max_lag)
+                return fail(ctx, TE_EINVAL, "variable lag outside 0..max_lag");
+        }
+    return TE_OK;
+}
+
+// ---- engine ----------------------------------------------------------------
+namespace {
+
+constexpr int kSMs = 152;
+
+struct ClassKey {
+    bool dx1;
+    bool k4;
+    bool operator<(const ClassKey &o) const
+    {
+        return std::tie(dx1, k4) < std::tie(o.dx1, o.k4);
+    }
+};
+
+long long count_ctas(const std::vector<const HostGroup *> &gs, int M)
+{
+    long long n = 0;
+    for (const HostGroup *g : gs) {
+        const long long N = g->data->T - g->max_lag;
+        const long long qt = (N + 127) / 128;
+        const long long mb = ((long long)g->members.size() + M - 1) / M;
+        n += qt * mb;
+    }
+    return n;
+}
+
+}  // namespace
+
+te_status run_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_out, int dbg_out,
+                     float *dbg_eps, int *dbg_nxz, int *dbg_nyz, int *dbg_nz)
+{
+    te_status st;
+    int max_N = 0;
+    for (const HostGroup &g : groups) max_N = std::max(max_N, g.data->T - g.max_lag);
+    if ((st = ensure_q(ctx, max_N + 1))) return st;
+    if ((st = ensure_dev(ctx, ctx->ws_acc, (size_t)std::max(n_out, 1) * 16))) return st;
+    if ((st = ensure_dev(ctx, ctx->ws_keys, (size_t)std::max(n_out, 1) * 16))) return st;
+    CK(cudaMemsetAsync(ctx->ws_acc.p, 0, (size_t)n_out * 16, ctx->stream), "cudaMemsetAsync");
+
+    std::map<ClassKey, std::vector<const HostGroup *>> classes;
+    for (const HostGroup &g : groups) {
+        if (g.members.empty()) continue;
+        classes[ClassKey{g.dx == 1, g.k == 4}].push_back(&g);
+    }
+
+    // host tables for every class, staged in one pinned block
+    struct Plan {
+        KsgVariant v;
+        bool dx1;
+        int jt;
+        size_t smem;
+        long long items;
+        size_t g_off, m_off, c_off;  // element offsets into the tables
+        int n_groups;
+    };
+    std::vector<Plan> plans;
+    std::vector<GroupDesc> gdesc;
+    std::vector<MemberDesc> mdesc;
+    std::vector<int> cols;
+    uint64_t pair_evals = 0, members_total = 0;
+
+    for (auto &kv : classes) {
+        const bool dx1 = kv.first.dx1, k4 = kv.first.k4;
+        auto &gs = kv.second;
+        KsgVariant v{4, 4, 128};
+        if (!k4) {
+            v = KsgVariant{2, 0, 128};
+        } else if (dx1) {
+            v.m = 16;
+            if (count_ctas(gs, 16) < 4LL * kSMs) v.m = 8;
+            if (v.m == 8 && count_ctas(gs, 8) < 4LL * kSMs) v.m = 4;
+        } else {
+            v.m = 4;
+        }
+        int rows_t = 0, rows_q = 0, maxN = 0;
+        for (const HostGroup *g : gs) {
+            const int dyz = (int)g->y.size() + (int)g->z.size();
+            rows_t = std::max(rows_t, dyz + v.m * g->dx);
+            rows_q = std::max(rows_q, dyz + (dx1 ? 0 : v.m * g->dx));
+            maxN = std::max(maxN, g->data->T - g->max_lag);
+        }
+        if (!dx1 && v.m > 2 && (size_t)4 * (rows_t * 64 + rows_q * 128) > 180 * 1024) {
+            v.m = 2;
+            rows_t = rows_q = 0;
+            for (const HostGroup *g : gs) {
+                const int dyz = (int)g->y.size() + (int)g->z.size();
+                rows_t = std::max(rows_t, dyz + v.m * g->dx);
+                rows_q = std::max(rows_q, dyz + v.m * g->dx);
+            }
+        }
+        auto jt_for = [&](size_t budget) {
+            long long room = (long long)budget / 4 - (long long)rows_q * 128;
+            long long jt = room / std::max(rows_t, 1);
+            jt &= ~7LL;
+            return (int)std::min<long long>(jt, 2048);
+        };
+        int jt = jt_for(40 * 1024);
+        if (jt < 64) jt = jt_for(190 * 1024);
+        if (jt < 8) return fail(ctx, TE_EINTERNAL, "shared-memory tile does not fit");
+        jt = std::min(jt, (maxN + 7) & ~7);
+
+        Plan p;
+        p.v = v;
+        p.dx1 = dx1;
+        p.jt = jt;
+        p.smem = 4 * ((size_t)rows_t * jt + (size_t)rows_q * 128);
+        p.g_off = gdesc.size();
+        p.m_off = mdesc.size();
+        p.c_off = cols.size();
+        p.n_groups = (int)gs.size();
+        long long item = 0;
+        for (const HostGroup *g : gs) {
+            const te_data *d = g->data;
+            const int N = d->T - g->max_lag;
+            auto off = [&](te_var vv) { return vv.proc * d->T + g->max_lag - vv.lag; };
+            GroupDesc gd{};
+            gd.base = d->d_series;
+            gd.N = N;
+            gd.k = g->k;
+            gd.theiler = g->theiler;
+            gd.dy = (int)g->y.size();
+            gd.dz = (int)g->z.size();
+            gd.dx = g->dx;
+            gd.ycol = (int)(cols.size() - p.c_off);
+            for (te_var vv : g->y) cols.push_back(off(vv));
+            gd.zcol = (int)(cols.size() - p.c_off);
+            for (te_var vv : g->z) cols.push_back(off(vv));
+            const int xbase = (int)(cols.size() - p.c_off);
+            for (te_var vv : g->xvars) cols.push_back(off(vv));
+            gd.member_begin = (int)(mdesc.size() - p.m_off);
+            gd.n_members = (int)g->members.size();
+            for (const HostMember &hm : g->members) {
+                MemberDesc md;
+                md.perm = hm.perm;
+                md.xcol = xbase + hm.xcol_first;
+                md.out = hm.out;
+                mdesc.push_back(md);
+            }
+            gd.n_qtiles = (N + 127) / 128;
+            gd.n_mblocks = (gd.n_members + v.m - 1) / v.m;
+            gd.item_begin = item;
+            item += (long long)gd.n_qtiles * gd.n_mblocks;
+            gdesc.push_back(gd);
+            pair_evals += (uint64_t)g->members.size() * 2ull * (uint64_t)N * (uint64_t)(N - 1);
+            members_total += g->members.size();
+        }
+        p.items = item;
+        plans.push_back(p);
+    }
+    if (plans.empty()) {
+        CK(launch_finalize((const unsigned long long *)ctx->ws_acc.p, (long long *)ctx->ws_keys.p,
+                           n_out, ctx->stream),
+           "finalize launch");
+        return TE_OK;
+    }
+
+    const size_t gbytes = gdesc.size() * sizeof(GroupDesc);
+    const size_t mbytes = mdesc.size() * sizeof(MemberDesc);
+    const size_t cbytes = cols.size() * sizeof(int);
+    if ((st = ensure_pin(ctx, gbytes + mbytes + cbytes + 64))) return st;
+    if ((st = ensure_dev(ctx, ctx->ws_groups, gbytes + 16))) return st;
+    if ((st = ensure_dev(ctx, ctx->ws_members, mbytes + 16))) return st;
+    if ((st = ensure_dev(ctx, ctx->ws_cols, cbytes + 16))) return st;
+    char *pin = (char *)ctx->pin;
+    std::memcpy(pin, gdesc.data(), gbytes);
+    std::memcpy(pin + gbytes, mdesc.data(), mbytes);
+    std::memcpy(pin + gbytes + mbytes, cols.data(), cbytes);
+    CK(copy_h2d(ctx, ctx->ws_groups.p, pin, gbytes), "cudaMemcpyAsync");
+    CK(copy_h2d(ctx, ctx->ws_members.p, pin + gbytes, mbytes), "cudaMemcpyAsync");
+    if (cbytes) CK(copy_h2d(ctx, ctx->ws_cols.p, pin + gbytes + mbytes, cbytes), "cudaMemcpyAsync");
+
+    if (!ctx->prepared) {
+        CK(ksg_prepare_attributes(), "cudaFuncSetAttribute");
+        ctx->prepared = 1;
+    }
+    CK(cudaEventRecord(ctx->ev_a, ctx->stream), "cudaEventRecord");
+    for (const Plan &p : plans) {
+        KsgLaunch L{};
+        L.groups = (const GroupDesc *)ctx->ws_groups.p + p.g_off;
+        L.n_groups = p.n_groups;
+        L.members = (const MemberDesc *)ctx->ws_members.p + p.m_off;
+        L.cols = (const int *)ctx->ws_cols.p + p.c_off;
+        L.q = ctx->q_dev;
+        L.acc = (unsigned long long *)ctx->ws_acc.p;
+        L.dbg_eps = dbg_eps;
+        L.dbg_nxz = dbg_nxz;
+        L.dbg_nyz = dbg_nyz;
+        L.dbg_nz = dbg_nz;
+        L.dbg_out = dbg_out;
+        L.jt = p.jt;
+        CK(launch_ksg(L, p.v, p.items, p.dx1, p.smem, ctx->stream), "KSG kernel launch");
+        ctx->stats.launches++;
+        ctx->stats.ksg_launches++;
+    }
+    CK(cudaEventRecord(ctx->ev_b, ctx->stream), "cudaEventRecord");
+    CK(launch_finalize((const unsigned long long *)ctx->ws_acc.p, (long long *)ctx->ws_keys.p,
+                       n_out, ctx->stream),
+       "finalize launch");
+    ctx->stats.launches++;
+    CK(cudaEventSynchronize(ctx->ev_b), "cudaEventSynchronize");
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev_a, ctx->ev_b), "cudaEventElapsedTime");
+    ctx->stats.kernel_ms += ms;
+    ctx->stats.pair_evals += pair_evals;
+    ctx->stats.estimates += members_total;
+    return TE_OK;
+}
+
+}  // namespace teksg
+
+// ---- C ABI -------------------------------------------------------------------
+
+#define GUARD_BEGIN try {
+#define GUARD_END                                                           \
+    }                                                                       \
+    catch (const std::bad_alloc &) {                                        \
+        return fail(ctx, TE_ENOMEM, "host allocation failed");              \
+    }                                                                       \
+    catch (...) {                                                           \
+        return fail(ctx, TE_EINTERNAL, "unexpected C++ exception");         \
+    }
+
+extern "C" {
+
+te_status te_ctx_create(int device, te_ctx **out)
+{
+    if (!out) return TE_EINVAL;
+    te_ctx *ctx = nullptr;
+    try {
+        ctx = new te_ctx();
+    } catch (...) {
+        return TE_ENOMEM;
+    }
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || device < 0 || device >= n) {
+        delete ctx;
+        return e != cudaSuccess ? TE_ECUDA : TE_EINVAL;
+    }
+    ctx->device = device;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&ctx->ev_a) != cudaSuccess || cudaEventCreate(&ctx->ev_b) != cudaSuccess) {
+        delete ctx;
+        return TE_ECUDA;
+    }
+    ctx->stream = ctx->own_stream;
+    *out = ctx;
+    return TE_OK;
+}
+
+te_status te_ctx_set_stream(te_ctx *ctx, void *cuda_stream)
+{
+    if (!ctx) return TE_EINVAL;
+    ctx->stream = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own_stream;
+    ctx->err.clear();
+    return TE_OK;
+}
+
+void te_ctx_destroy(te_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    DevBuf *bufs[] = {&ctx->ws_groups, &ctx->ws_members, &ctx->ws_cols, &ctx->ws_acc,
+                      &ctx->ws_keys,   &ctx->ws_perm,    &ctx->ws_stat, &ctx->ws_dbg};
+    for (DevBuf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (ctx->q_dev) cudaFree(ctx->q_dev);
+    if (ctx->pin) cudaFreeHost(ctx->pin);
+    if (ctx->ev_a) cudaEventDestroy(ctx->ev_a);
+    if (ctx->ev_b) cudaEventDestroy(ctx->ev_b);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    delete ctx;
+}
+
+const char *te_last_error(const te_ctx *ctx)
+{
+    if (!ctx) return "no context";
+    return ctx->err.c_str();
+}
+
+te_status te_data_create(te_ctx *ctx, const float *series, int32_t n_proc, int32_t T,
+                         int series_on_device, te_data **out)
+{
+    if (!ctx) return TE_EINVAL;
+    GUARD_BEGIN
+    ctx->err.clear();
+    if (!series || !out) return fail(ctx, TE_EINVAL, "series or out is NULL");
+    if (n_proc < 1 || T < 2) return fail(ctx, TE_EINVAL, "need n_proc >= 1 and T >= 2");
+    if ((long long)n_proc * T >= (1LL << 31))
+        return fail(ctx, TE_EINVAL, "n_proc * T must be below 2^31");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const size_t bytes = (size_t)n_proc * T * sizeof(float);
+    float *d = nullptr;
+    CK(cudaMalloc(&d, bytes + sizeof(int)), "cudaMalloc");
+    cudaError_t e = series_on_device
+                        ? cudaMemcpyAsync(d, series, bytes, cudaMemcpyDeviceToDevice, ctx->stream)
+                        : copy_h2d(ctx, d, series, bytes);
+    int *flag = (int *)((char *)d + bytes);
+    int hflag = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = launch_check_finite(d, (long long)n_proc * T, flag, ctx->stream);
+    if (e == cudaSuccess) e = copy_d2h(ctx, &hflag, flag, sizeof(int));
+    ctx->stats.launches++;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(ctx, e, "te_data_create upload");
+    }
+    if (hflag) {
+        cudaFree(d);
+        return fail(ctx, TE_EINVAL, "series holds a non-finite value");
+    }
+    te_data *D = new te_data{ctx, d, n_proc, T};
+    *out = D;
+    return TE_OK;
+    GUARD_END
+}
+
+void te_data_destroy(te_data *data)
+{
+    if (!data) return;
+    cudaSetDevice(data->ctx->device);
+    cudaStreamSynchronize(data->ctx->stream);
+    cudaFree(data->d_series);
+    delete data;
+}
+
+static te_status cmi_common(te_ctx *ctx, const te_data *data, const te_var *x, int32_t dx,
+                            const te_var *y, int32_t dy, const te_var *z, int32_t dz,
+                            const te_ksg_params *p, double *out_cmi, int64_t *out_key,
+                            int32_t dbg_member, float *eps, int32_t *nxz, int32_t *nyz,
+                            int32_t *nz)
+{
+    te_status st;
+    if (!p) return fail(ctx, TE_EINVAL, "params is NULL");
+    if ((st = validate_estimate(ctx, data, x, dx, y, dy, z, dz, p->k, p->theiler, p->max_lag,
+                                p->n_surr)))
+        return st;
+    if (dbg_member >= 0 && dbg_member > p->n_surr)
+        return fail(ctx, TE_EINVAL, "member outside 0..n_surr");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const int N = data->T - p->max_lag;
+    const int S = p->n_surr;
+    if ((st = ensure_dev(ctx, ctx->ws_perm, (size_t)std::max(S, 1) * N * sizeof(int32_t))))
+        return st;
+    int32_t *perm = (int32_t *)ctx->ws_perm.p;
+    CK(launch_perms(perm, N, N, p->seed, p->stream_tag, 0, 0, 1, S, ctx->stream),
+       "permutation launch");
+    if (S > 0) ctx->stats.launches++;
+    HostGroup g;
+    g.data = data;
+    g.max_lag = p->max_lag;
+    g.k = p->k;
+    g.theiler = p->theiler;
+    g.y.assign(y, y + dy);
+    if (dz) g.z.assign(z, z + dz);
+    g.dx = dx;
+    g.xvars.assign(x, x + dx);
+    for (int s = 0; s <= S; ++s)
+        g.members.push_back(HostMember{0, s == 0 ? nullptr : perm + (size_t)(s - 1) * N, s});
+    std::vector<HostGroup> gs{g};
+    float *d_eps = nullptr;
+    int *d_cnt = nullptr;
+    if (dbg_member >= 0) {
+        if ((st = ensure_dev(ctx, ctx->ws_dbg, (size_t)N * 16))) return st;
+        d_eps = (float *)ctx->ws_dbg.p;
+        d_cnt = (int *)((char *)ctx->ws_dbg.p + (size_t)N * 4);
+    }
+    if ((st = run_groups(ctx, gs, S + 1, dbg_member, d_eps, d_cnt, d_cnt + N, d_cnt + 2 * N)))
+        return st;
+    if (dbg_member >= 0) {
+        if (eps)
+            CK(copy_d2h(ctx, eps, d_eps, (size_t)N * 4), "cudaMemcpyAsync");
+        if (nxz)
+            CK(copy_d2h(ctx, nxz, d_cnt, (size_t)N * 4), "cudaMemcpyAsync");
+        if (nyz)
+            CK(copy_d2h(ctx, nyz, d_cnt + N, (size_t)N * 4), "cudaMemcpyAsync");
+        if (nz)
+            CK(copy_d2h(ctx, nz, d_cnt + 2 * N, (size_t)N * 4), "cudaMemcpyAsync");
+        CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+        return TE_OK;
+    }
+    std::vector<int64_t> keys((size_t)2 * (S + 1));
+    CK(copy_d2h(ctx, keys.data(), ctx->ws_keys.p, keys.size() * 8), "cudaMemcpyAsync");
+    CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    for (int s = 0; s <= S; ++s)
+        out_cmi[s] = key_to_cmi(ctx, keys[2 * s], (uint64_t)keys[2 * s + 1], p->k, N);
+    if (out_key) std::memcpy(out_key, keys.data(), keys.size() * 8);
+    return TE_OK;
+}
+
+te_status cmi_ksg(te_ctx *ctx, const te_data *data, const te_var *x, int32_t dx, const te_var *y,
+                  int32_t dy, const te_var *z, int32_t dz, const te_ksg_params *params,
+                  double *out_cmi, int64_t *out_key)
+{
+    if (!ctx) return TE_EINVAL;
+    GUARD_BEGIN
+    ctx->err.clear();
+    if (!out_cmi) return fail(ctx, TE_EINVAL, "out_cmi is NULL");
+    return cmi_common(ctx, data, x, dx, y, dy, z, dz, params, out_cmi, out_key, -1, nullptr,
+                      nullptr, nullptr, nullptr);
+    GUARD_END
+}
+
+te_status cmi_ksg_debug(te_ctx *ctx, const te_data *data, const te_var *x, int32_t dx,
+                        const te_var *y, int32_t dy, const te_var *z, int32_t dz,
+                        const te_ksg_params *params, int32_t member, float *eps, int32_t *n_xz,
+                        int32_t *n_yz, int32_t *n_z)
+{
+    if (!ctx) return TE_EINVAL;
+    GUARD_BEGIN
+    ctx->err.clear();
+    if (member < 0) return fail(ctx, TE_EINVAL, "member must be >= 0");
+    return cmi_common(ctx, data, x, dx, y, dy, z, dz, params, nullptr, nullptr, member, eps,
+                      n_xz, n_yz, n_z);
+    GUARD_END
+}
+
+te_status cmi_ksg_batch(te_ctx *ctx, const te_cmi_job *jobs, int32_t n_jobs, double *out,
+                        int64_t *out_key)
+{
+    if (!ctx) return TE_EINVAL;
+    GUARD_BEGIN
+    ctx->err.clear();
+    te_status st;
+    if (n_jobs < 0 || (n_jobs > 0 && (!jobs || !out)))
+        return fail(ctx, TE_EINVAL, "jobs or out is NULL");
+    if (n_jobs == 0) return TE_OK;
+    size_t perm_elems = 0;
+    int n_out = 0;
+    std::vector<int> job_out(n_jobs), job_N(n_jobs);
+    std::vector<size_t> job_perm(n_jobs);
+    for (int j = 0; j < n_jobs; ++j) {
+        const te_cmi_job &J = jobs[j];
+        if ((st = validate_estimate(ctx, J.data, J.x, J.dx, J.y, J.dy, J.z, J.dz, J.params.k,
+                                    J.params.theiler, J.params.max_lag, J.params.n_surr))) {
+            ctx->err = "job " + std::to_string(j) + ": " + ctx->err;
+            return st;
+        }
+        job_N[j] = J.data->T - J.params.max_lag;
+        job_out[j] = n_out;
+        n_out += 1 + J.params.n_surr;
+        job_perm[j] = perm_elems;
+        perm_elems += (size_t)J.params.n_surr * job_N[j];
+    }
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if ((st = ensure_dev(ctx, ctx->ws_perm, std::max<size_t>(perm_elems, 1) * 4))) return st;
+    int32_t *perm = (int32_t *)ctx->ws_perm.p;
+    // jobs with the same data, point set, k, window, Y and Z share a group
+    std::map<std::vector<long long>, int> gid;
+    std::vector<HostGroup> groups;
+    for (int j = 0; j < n_jobs; ++j) {
+        const te_cmi_job &J = jobs[j];
+        const int N = job_N[j], S = J.params.n_surr;
+        CK(launch_perms(perm + job_perm[j], N, N, J.params.seed, J.params.stream_tag, 0, 0, 1, S,
+                        ctx->stream),
+           "permutation launch");
+        if (S > 0) ctx->stats.launches++;
+        std::vector<long long> key{(long long)(uintptr_t)J.data, J.params.max_lag, J.params.k,
+                                   J.params.theiler, J.dx, J.dy, J.dz};
+        for (int d = 0; d < J.dy; ++d) key.push_back(((long long)J.y[d].proc << 32) | J.y[d].lag);
+        key.push_back(-1);
+        for (int d = 0; d < J.dz; ++d) key.push_back(((long long)J.z[d].proc << 32) | J.z[d].lag);
+        auto it = gid.find(key);
+        int g;
+        if (it == gid.end()) {
+            g = (int)groups.size();
+            gid[key] = g;
+            HostGroup hg;
+            hg.data = J.data;
+            hg.max_lag = J.params.max_lag;
+            hg.k = J.params.k;
+            hg.theiler = J.params.theiler;
+            hg.y.assign(J.y, J.y + J.dy);
+            if (J.dz) hg.z.assign(J.z, J.z + J.dz);
+            hg.dx = J.dx;
+            groups.push_back(hg);
+        } else {
+            g = it->second;
+        }
+        HostGroup &hg = groups[g];
+        const int xfirst = (int)hg.xvars.size();
+        hg.xvars.insert(hg.xvars.end(), J.x, J.x + J.dx);
+        for (int s = 0; s <= S; ++s)
+            hg.members.push_back(HostMember{
+                xfirst, s == 0 ? nullptr : perm + job_perm[j] + (size_t)(s - 1) * N,
+                job_out[j] + s});
+    }
+    if ((st = run_groups(ctx, groups, n_out))) return st;
+    std::vector<int64_t> keys((size_t)2 * n_out);
+    CK(copy_d2h(ctx, keys.data(), ctx->ws_keys.p, keys.size() * 8), "cudaMemcpyAsync");
+    CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    for (int j = 0; j < n_jobs; ++j)
+        for (int s = 0; s <= jobs[j].params.n_surr; ++s) {
+            const int o = job_out[j] + s;
+            out[o] = key_to_cmi(ctx, keys[2 * o], (uint64_t)keys[2 * o + 1], jobs[j].params.k,
+                                job_N[j]);
+        }
+    if (out_key) std::memcpy(out_key, keys.data(), keys.size() * 8);
+    return TE_OK;
+    GUARD_END
+}
+
+te_status te_get_stats(const te_ctx *ctx, te_stats *out)
+{
+    if (!ctx || !out) return TE_EINVAL;
+    *out = ctx->stats;
+    return TE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// Host-side runtime shared by the C-ABI translation units (not public).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/te_ksg.h"
+#include "ksg_internal.h"
+
+namespace teksg {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+struct HostMember {
+    int xcol_first;           // index into the job's column list
+    const int32_t *perm;      // device permutation or nullptr
+    int out;                  // output slot
+};
+
+// One group = members sharing data, point set, k, theiler, Y and Z.
+struct HostGroup {
+    const te_data *data = nullptr;
+    int max_lag = 0;
+    int k = 4, theiler = 0;
+    std::vector<te_var> y, z;
+    int dx = 1;
+    std::vector<te_var> xvars;     // dx variables per member, member-major
+    std::vector<HostMember> members;
+};
+
+struct te_status_error {
+    te_status st;
+    std::string msg;
+};
+
+}  // namespace teksg
+
+struct te_data {
+    te_ctx *ctx;
+    float *d_series;
+    int32_t n_proc, T;
+};
+
+struct te_ctx {
+    int device = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    // digamma fixed-point table Q[0..q_len) on the device, built on the host in
+    // double-double arithmetic (psi(n) = -gamma + H_{n-1}).
+    std::vector<int64_t> q_host;
+    double dd_hi = 0.0, dd_lo = 0.0;   // running psi(q_host.size() - 1) in double-double
+    int64_t *q_dev = nullptr;
+    int q_dev_len = 0;
+    // grow-only device workspaces
+    teksg::DevBuf ws_groups, ws_members, ws_cols, ws_acc, ws_keys, ws_perm, ws_stat, ws_dbg;
+    // pinned host staging
+    void *pin = nullptr;
+    size_t pin_cap = 0;
+    te_stats stats{};
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    int prepared = 0;
+};
+
+namespace teksg {
+
+// status helpers; CK returns from the calling function on a CUDA error
+#define CK(call, what)                                                  \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return ::teksg::cuda_fail(ctx, e_, what); \
+    } while (0)
+
+te_status fail(te_ctx *ctx, te_status st, const std::string &msg);
+te_status cuda_fail(te_ctx *ctx, cudaError_t e, const char *what);
+
+te_status ensure_dev(te_ctx *ctx, DevBuf &b, size_t bytes);
+te_status ensure_pin(te_ctx *ctx, size_t bytes);
+te_status ensure_q(te_ctx *ctx, int n_needed);   // Q[0..n_needed] on the device
+
+// cudaMemcpyAsync on the context's stream, counted in ctx->stats
+cudaError_t copy_h2d(te_ctx *ctx, void *dst, const void *src, size_t bytes);
+cudaError_t copy_d2h(te_ctx *ctx, void *dst, const void *src, size_t bytes);
+
+// Validate one estimate's variables against its data and parameters.
+te_status validate_estimate(te_ctx *ctx, const te_data *data, const te_var *x, int dx,
+                            const te_var *y, int dy, const te_var *z, int dz, int k, int theiler,
+                            int max_lag, int n_surr);
+
+// Run every group in fused launches; keys of all n_out slots end up in
+// ctx->ws_keys as int64 pairs (hi, lo).  Slots not written by any member are 0.
+te_status run_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_out,
+                     int dbg_out = -1, float *dbg_eps = nullptr, int *dbg_nxz = nullptr,
+                     int *dbg_nyz = nullptr, int *dbg_nz = nullptr);
+
+double key_to_cmi(const te_ctx *ctx, int64_t hi, uint64_t lo, int k, int N);
+
+}  // namespace teksg
