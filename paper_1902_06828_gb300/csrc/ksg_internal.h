@@ -22,7 +22,29 @@ struct GroupDesc {
     int n_qtiles;           // ceil(N / query tile)
     int n_mblocks;          // ceil(n_members / members per thread)
     long long item_begin;   // first CTA of the group in the launch
+    // Spatial order (nullptr sigma = time order).  Points are processed in the
+    // order of a Morton curve over the shared (Y, Z) coordinates: position p is
+    // time point sigma[p]; yz[d * N + p] holds Y (d < dy) and Z coordinates in
+    // that order; box[d * n_chunks8 + c] = (min, max) of dim d over positions
+    // 8c .. 8c + 7.  Only used with theiler == 0.
+    const int *sigma;
+    const float *yz;
+    const float2 *box;
+    int n_chunks8;
 };
+
+// One spatial-order job (one CTA): Morton keys of the (Y, Z) coordinates of a
+// group, sorted in shared memory; writes sigma, yz and box as described above.
+struct OrderJob {
+    const float *base;
+    int N, dyz;
+    int cols[32];           // column offsets of Y then Z
+    int *sigma;
+    float *yz;
+    float2 *box;
+};
+constexpr int kMaxOrderN = 16384;   // points a CTA can sort in shared memory
+cudaError_t launch_order(const OrderJob *jobs, int n_jobs, cudaStream_t st);
 
 struct MemberDesc {
     const int32_t *perm;    // device permutation of [0, N) applied to X, or nullptr
@@ -55,8 +77,16 @@ struct KsgVariant {
 
 cudaError_t launch_ksg(const KsgLaunch &L, const KsgVariant &v, long long n_items, bool dx1,
                        size_t smem_bytes, cudaStream_t st);
-size_t ksg_smem_bytes(const KsgVariant &v, int dy, int dz, int dx, bool dx1, int jt);
 cudaError_t ksg_prepare_attributes();
+
+// dynamic shared memory of the fused kernel: the staged tile, the query-side
+// values, per-warp chunk bounds, the staged index row and the per-thread
+// (d_Z, d_YZ) scratch of one 8-point chunk
+inline size_t ksg_smem_bytes(int rows_t, int rows_q, int jt, int qt)
+{
+    return 4 * ((size_t)rows_t * jt + (size_t)rows_q * qt) + 8 * (size_t)(qt / 32) * (jt / 8) +
+           4 * (size_t)jt + 8 * 8 * (size_t)qt;
+}
 
 // Fisher-Yates permutations of [0, n), one per surrogate s = s_first .. s_first +
 // n_perm - 1, keyed by SplitMix64 over (seed, target, stage, iter, s).

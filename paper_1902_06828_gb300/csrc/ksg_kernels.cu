@@ -58,6 +58,42 @@ __device__ __forceinline__ void load8(const float *p, float (&v)[JC])
     v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
 }
 
+// M staged X values of one point (members are the fastest index of the tile).
+template <int M>
+__device__ __forceinline__ void load_members(const float *p, float (&v)[M])
+{
+    if (M % 4 == 0) {
+#pragma unroll
+        for (int a = 0; a < M; a += 4) {
+            const float4 t = *reinterpret_cast<const float4 *>(p + a);
+            v[a] = t.x; v[a + 1] = t.y; v[a + 2] = t.z; v[a + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < M; a += 2) {
+            const float2 t = *reinterpret_cast<const float2 *>(p + a);
+            v[a] = t.x; v[a + 1] = t.y;
+        }
+    }
+}
+
+// Strict range counts of one pair for one member, counters in float (exact
+// below 2^24): n_z += d_Z < e; n_xz += d_Z < e and d_X < e; n_yz += d_YZ < e.
+// The compares run on the ALU pipe, the predicated adds on the FMA pipe.
+__device__ __forceinline__ void count3(float &cz, float &cxz, float &cyz, float dz, float dyz,
+                                       float dc, float e)
+{
+    asm("{\n\t.reg .pred pz, pxz, pyz;\n\t"
+        "setp.lt.f32 pz, %3, %6;\n\t"
+        "setp.lt.and.f32 pxz, %5, %6, pz;\n\t"
+        "setp.lt.f32 pyz, %4, %6;\n\t"
+        "@pz add.f32 %0, %0, 0f3F800000;\n\t"
+        "@pxz add.f32 %1, %1, 0f3F800000;\n\t"
+        "@pyz add.f32 %2, %2, 0f3F800000;\n\t}"
+        : "+f"(cz), "+f"(cxz), "+f"(cyz)
+        : "f"(dz), "f"(dyz), "f"(dc), "f"(e));
+}
+
 // Shared-subspace distances for JC consecutive staged points starting at c:
 // dzv = max over Z dims (-inf if dz == 0), dyzv = max(dzv, max over Y dims).
 __device__ __forceinline__ void shared_dist(const float *tile, const float *qv, int jt, int dy,
@@ -100,10 +136,25 @@ __device__ __forceinline__ void member_dist(const float *tile, const float *qv, 
     }
 }
 
+__device__ __forceinline__ float warp_max(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_min(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
 template <int M, int KT, bool DX1>
 __global__ void __launch_bounds__(QT) ksg_fused_kernel(const KsgLaunch L)
 {
     constexpr int KB = KT > 0 ? KT : KMAX;
+    constexpr int NW = QT / 32;
     extern __shared__ __align__(16) float smem[];
 
     // ---- decode the work item: group, member block, query tile ----
@@ -119,71 +170,138 @@ __global__ void __launch_bounds__(QT) ksg_fused_kernel(const KsgLaunch L)
     const int mb = (int)(local / G.n_qtiles);
     const int qtile = (int)(local % G.n_qtiles);
     const int N = G.N, dy = G.dy, dz = G.dz, dx = G.dx, w = G.theiler;
+    const int dyz = dy + dz;
     const int k = KT > 0 ? KT : G.k;
     const int jt = L.jt;
+    const int cpt = jt >> 3;                  // chunks of 8 per tile
     const float *__restrict__ base = G.base;
+    const bool sorted = G.sigma != nullptr;   // Morton order over (Y, Z), theiler == 0
 
-    const int rows_t = dy + dz + M * dx;
-    float *tile = smem;                       // [rows_t][jt]
-    float *qv = smem + rows_t * jt;           // [rows_q][QT]
+    const int rows_t = dyz + M * dx;
+    const int rows_q = dyz + (DX1 ? 0 : M * dx);
+    float *tile = smem;                                    // [rows_t][jt]
+    float *qv = smem + rows_t * jt;                        // [rows_q][QT]
+    float2 *wlb = reinterpret_cast<float2 *>(qv + rows_q * QT);   // [NW][cpt] chunk bounds
+    int *sidx = reinterpret_cast<int *>(wlb + NW * cpt);  // [jt] staged point indices
+    float2 *scr = reinterpret_cast<float2 *>(sidx + jt) + threadIdx.x;  // [JC][QT] (d_Z, d_YZ)
+    float *tx = tile + dyz * jt;   // X part of the tile: [jt][M] (DX1) or [M*dx][jt]
     __shared__ const int32_t *s_perm[M];
+    __shared__ int s_xoff[M];
     __shared__ int s_out[M];
     __shared__ int s_valid[M];
+    __shared__ int s_shared_perm;
+    __shared__ float2 s_wbox[NW][32];
+    __shared__ int s_live[2][NW];
 
     const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const int i = qtile * QT + tid;
     const bool qvalid = i < N;
     const int ic = qvalid ? i : N - 1;
     const int qlo = qtile * QT;
     const int qhi = min(qlo + QT, N) - 1;
+    const int ti = sorted ? G.sigma[ic] : ic;   // time index of the query point
 
     if (tid < M) {
         const int mi = mb * M + tid;
         const int mc = mi < G.n_members ? mi : G.n_members - 1;
         const MemberDesc md = L.members[G.member_begin + mc];
         s_perm[tid] = md.perm;
+        s_xoff[tid] = L.cols[md.xcol];
         s_out[tid] = md.out;
         s_valid[tid] = mi < G.n_members;
     }
     __syncthreads();
+    if (tid == 0) {
+        int same = 1;
+        for (int m = 1; m < M; ++m) same &= (s_perm[m] == s_perm[0]);
+        s_shared_perm = same;
+    }
+
+    auto yz_off = [&](int d) {
+        return d < dy ? L.cols[G.ycol + d] : L.cols[G.zcol + d - dy];
+    };
 
     // query-side values
-    for (int d = 0; d < dy; ++d) qv[d * QT + tid] = base[L.cols[G.ycol + d] + ic];
-    for (int d = 0; d < dz; ++d) qv[(dy + d) * QT + tid] = base[L.cols[G.zcol + d] + ic];
+    for (int d = 0; d < dyz; ++d)
+        qv[d * QT + tid] = sorted ? G.yz[(size_t)d * N + ic] : base[yz_off(d) + ic];
     float xi[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) {
         const int mi = min(mb * M + m, G.n_members - 1);
         const MemberDesc md = L.members[G.member_begin + mi];
-        const int pi = md.perm ? md.perm[ic] : ic;
+        const int pi = md.perm ? md.perm[ti] : ti;
         if (DX1) {
             xi[m] = base[L.cols[md.xcol] + pi];
         } else {
             xi[m] = 0.f;
             for (int d = 0; d < dx; ++d)
-                qv[(dy + dz + m * dx + d) * QT + tid] = base[L.cols[md.xcol + d] + pi];
+                qv[(dyz + m * dx + d) * QT + tid] = base[L.cols[md.xcol + d] + pi];
         }
     }
+    // per-warp bounding box of the query points in (Y, Z)
+    if (sorted) {
+        for (int d = 0; d < dyz; ++d) {
+            const float v = qv[d * QT + tid];
+            const float mn = warp_min(v), mx = warp_max(v);
+            if (lane == 0) s_wbox[warp][d] = make_float2(mn, mx);
+        }
+    }
+    __syncthreads();
+    const bool shared_perm = s_shared_perm != 0;
+    const int32_t *perm0 = s_perm[0];
 
     auto stage = [&](int j0) {
-        for (int r = 0; r < rows_t; ++r) {
-            int off;
-            const int32_t *perm = nullptr;
-            if (r < dy) {
-                off = L.cols[G.ycol + r];
-            } else if (r < dy + dz) {
-                off = L.cols[G.zcol + r - dy];
-            } else {
-                const int m = (r - dy - dz) / dx, d = (r - dy - dz) - m * dx;
-                const int mi = min(mb * M + m, G.n_members - 1);
-                off = L.cols[L.members[G.member_begin + mi].xcol + d];
-                perm = s_perm[m];
-            }
+        const bool use_idx = sorted || shared_perm;
+        if (use_idx) {
             for (int jj = tid; jj < jt; jj += QT) {
                 const int j = j0 + jj;
+                int t = 0;
+                if (j < N) {
+                    t = sorted ? G.sigma[j] : j;
+                    if (shared_perm && perm0) t = perm0[t];
+                }
+                sidx[jj] = t;
+            }
+        }
+        for (int r = 0; r < dyz; ++r) {
+            const int off = sorted ? 0 : yz_off(r);
+            const float *src = sorted ? G.yz + (size_t)r * N : base + off;
+            for (int jj = tid; jj < jt; jj += QT) {
+                const int j = j0 + jj;
+                tile[r * jt + jj] = j < N ? src[j] : 0.f;
+            }
+        }
+        if (use_idx) __syncthreads();
+        if (DX1) {
+            for (int e = tid; e < jt * M; e += QT) {
+                const int jj = e / M, m = e - jj * M;
+                const int j = j0 + jj;
                 float v = 0.f;
-                if (j < N) v = base[off + (perm ? perm[j] : j)];
-                tile[r * jt + jj] = v;
+                if (j < N) {
+                    int t = use_idx ? sidx[jj] : j;
+                    const int32_t *perm = shared_perm ? nullptr : s_perm[m];
+                    if (perm) t = perm[t];
+                    v = base[s_xoff[m] + t];
+                }
+                tx[e] = v;
+            }
+        } else {
+            for (int r = dyz; r < rows_t; ++r) {
+                const int m = (r - dyz) / dx, d = (r - dyz) - m * dx;
+                const int mi = min(mb * M + m, G.n_members - 1);
+                const int off = L.cols[L.members[G.member_begin + mi].xcol + d];
+                const int32_t *perm = shared_perm ? nullptr : s_perm[m];
+                for (int jj = tid; jj < jt; jj += QT) {
+                    const int j = j0 + jj;
+                    float v = 0.f;
+                    if (j < N) {
+                        int t = use_idx ? sidx[jj] : j;
+                        if (perm) t = perm[t];
+                        v = base[off + t];
+                    }
+                    tile[r * jt + jj] = v;
+                }
             }
         }
     };
@@ -205,6 +323,32 @@ __global__ void __launch_bounds__(QT) ksg_fused_kernel(const KsgLaunch L)
         }
     };
 
+    // Lower bounds on d_YZ and d_Z between this warp's query points and each
+    // chunk of 8 points of the tile at j0 (sorted mode).  Exact float bounds:
+    // rounding is monotone, so fl(z_j - z_i) >= fl(min_chunk - max_query).
+    // Returns whether any chunk can still matter for this warp.
+    auto chunk_bounds = [&](int j0, int jn, bool pass1, float bound) {
+        const int nct = (jn + 7) >> 3;
+        bool live = false;
+        for (int c = lane; c < nct; c += 32) {
+            const int gc = (j0 >> 3) + c;
+            float lyz = 0.f, lz = 0.f;
+            for (int d = 0; d < dyz; ++d) {
+                const float2 b = G.box[(size_t)d * G.n_chunks8 + gc];
+                const float2 q = s_wbox[warp][d];
+                const float gap = fmaxf(fmaxf(__fsub_rn(b.x, q.y), __fsub_rn(q.x, b.y)), 0.f);
+                lyz = fmaxf(lyz, gap);
+                if (d >= dy) lz = fmaxf(lz, gap);
+            }
+            wlb[warp * cpt + c] = make_float2(lyz, lz);
+            live |= pass1 ? (lyz < bound) : (lz < bound);
+        }
+        __syncwarp();
+        return __any_sync(0xffffffffu, live);
+    };
+
+    const int ntiles = (N + jt - 1) / jt;
+
     // ---------------- pass 1: k nearest joint distances ----------------
     float buf[M][KB];
     float thr[M];
@@ -214,93 +358,159 @@ __global__ void __launch_bounds__(QT) ksg_fused_kernel(const KsgLaunch L)
         for (int a = 0; a < KB; ++a) buf[m][a] = CUDART_INF_F;
         thr[m] = CUDART_INF_F;
     }
-
-    for (int j0 = 0; j0 < N; j0 += jt) {
-        __syncthreads();
-        stage(j0);
-        __syncthreads();
-        const int jn = min(jt, N - j0);
-        for (int c = 0; c < jn; c += JC) {
-            float dzv[JC], dyzv[JC];
-            shared_dist(tile, qv, jt, dy, dz, c, dzv, dyzv);
-            if (needs_mask(j0 + c)) apply_mask(j0 + c, dzv, dyzv);
+    float tmax_w = CUDART_INF_F;   // max over the warp's lanes and members of thr
+    {
+        // sorted mode: start at this CTA's own tile and spiral outwards
+        const int home = sorted ? min(qlo / jt, ntiles - 1) : 0;
+        int up = home + 1, down = home - 1;
+        bool toggle = true;
+        for (int s = 0; s < ntiles; ++s) {
+            int t;
+            if (s == 0) t = home;
+            else if ((toggle && up < ntiles) || down < 0) t = up++;
+            else t = down--;
+            toggle = !toggle;
+            const int j0 = t * jt;
+            const int jn = min(jt, N - j0);
+            if (sorted) {
+                const bool live = chunk_bounds(j0, jn, true, tmax_w);
+                if (lane == 0) s_live[s & 1][warp] = live;
+            }
+            __syncthreads();
+            if (sorted) {
+                int any = 0;
 #pragma unroll
-            for (int m = 0; m < M; ++m) {
-                float dcv[JC];
+                for (int a = 0; a < NW; ++a) any |= s_live[s & 1][a];
+                if (!any) continue;
+            }
+            stage(j0);
+            __syncthreads();
+            for (int c = 0; c < jn; c += JC) {
+                if (sorted && wlb[warp * cpt + (c >> 3)].x >= tmax_w) continue;
+                float dzv[JC], dyzv[JC];
+                shared_dist(tile, qv, jt, dy, dz, c, dzv, dyzv);
+                if (needs_mask(j0 + c)) apply_mask(j0 + c, dzv, dyzv);
                 if (DX1) {
-                    float xj[JC];
-                    load8(tile + (dy + dz + m) * jt + c, xj);
+                    // members unrolled, the chunk's points in a loop: compact hot code
 #pragma unroll
-                    for (int u = 0; u < JC; ++u) dcv[u] = fabsf(__fsub_rn(xi[m], xj[u]));
+                    for (int u = 0; u < JC; ++u) scr[u * QT] = make_float2(dzv[u], dyzv[u]);
+#pragma unroll 1
+                    for (int u = 0; u < JC; ++u) {
+                        const float dyzu = scr[u * QT].y;
+                        float xv[M];
+                        load_members<M>(tx + (c + u) * M, xv);
+#pragma unroll
+                        for (int m = 0; m < M; ++m) {
+                            const float D = fmaxf(fabsf(__fsub_rn(xi[m], xv[m])), dyzu);
+                            if (D < thr[m]) {
+                                topk_insert<KB>(buf[m], D);
+                                thr[m] = KT > 0 ? buf[m][KB - 1] : topk_at<KB>(buf[m], k - 1);
+                            }
+                        }
+                    }
                 } else {
-                    member_dist<M>(tile, qv, jt, dy, dz, dx, m, c, dcv);
-                }
 #pragma unroll
-                for (int u = 0; u < JC; ++u) {
-                    const float D = fmaxf(dcv[u], dyzv[u]);
-                    if (D < thr[m]) {
-                        topk_insert<KB>(buf[m], D);
-                        thr[m] = KT > 0 ? buf[m][KB - 1] : topk_at<KB>(buf[m], k - 1);
+                    for (int m = 0; m < M; ++m) {
+                        float dcv[JC];
+                        member_dist<M>(tile, qv, jt, dy, dz, dx, m, c, dcv);
+#pragma unroll
+                        for (int u = 0; u < JC; ++u) {
+                            const float D = fmaxf(dcv[u], dyzv[u]);
+                            if (D < thr[m]) {
+                                topk_insert<KB>(buf[m], D);
+                                thr[m] = KT > 0 ? buf[m][KB - 1] : topk_at<KB>(buf[m], k - 1);
+                            }
+                        }
                     }
                 }
             }
+            if (sorted) {
+                float tm = thr[0];
+#pragma unroll
+                for (int m = 1; m < M; ++m) tm = fmaxf(tm, thr[m]);
+                tmax_w = warp_max(tm);
+            }
+            __syncthreads();
         }
     }
 
     // ---------------- pass 2: strict range counts ----------------
     float eps[M];
-    int cxz[M], cyz[M], cz[M];
+    float cxz[M], cyz[M], cz[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) {
         eps[m] = thr[m];
-        cxz[m] = cyz[m] = cz[m] = 0;
+        cxz[m] = cyz[m] = cz[m] = 0.f;
     }
-    for (int j0 = 0; j0 < N; j0 += jt) {
-        if (N > jt || j0 > 0) {
-            __syncthreads();
-            stage(j0);
-            __syncthreads();
-        }
+    const bool prune2 = sorted && dz > 0;   // with empty Z every j counts in n_xz
+    float emax_w = CUDART_INF_F;
+    if (prune2) {
+        float em = eps[0];
+#pragma unroll
+        for (int m = 1; m < M; ++m) em = fmaxf(em, eps[m]);
+        emax_w = warp_max(em);
+    }
+    for (int t = 0; t < ntiles; ++t) {
+        const int j0 = t * jt;
         const int jn = min(jt, N - j0);
+        if (prune2) {
+            const bool live = chunk_bounds(j0, jn, false, emax_w);
+            if (lane == 0) s_live[t & 1][warp] = live;
+        }
+        __syncthreads();
+        if (prune2) {
+            int any = 0;
+#pragma unroll
+            for (int a = 0; a < NW; ++a) any |= s_live[t & 1][a];
+            if (!any) continue;
+        }
+        stage(j0);
+        __syncthreads();
         for (int c = 0; c < jn; c += JC) {
+            if (prune2 && wlb[warp * cpt + (c >> 3)].y >= emax_w) continue;
             float dzv[JC], dyzv[JC];
             shared_dist(tile, qv, jt, dy, dz, c, dzv, dyzv);
             if (needs_mask(j0 + c)) apply_mask(j0 + c, dzv, dyzv);
+            // d_Z is -inf for valid pairs when Z is empty and +inf for masked
+            // pairs, so n_z also counts exactly the valid j in that case
+            if (DX1) {
 #pragma unroll
-            for (int m = 0; m < M; ++m) {
-                float dcv[JC];
-                if (DX1) {
-                    float xj[JC];
-                    load8(tile + (dy + dz + m) * jt + c, xj);
-#pragma unroll
-                    for (int u = 0; u < JC; ++u) dcv[u] = fabsf(__fsub_rn(xi[m], xj[u]));
-                } else {
-                    member_dist<M>(tile, qv, jt, dy, dz, dx, m, c, dcv);
-                }
-                const float e = eps[m];
-#pragma unroll
+                for (int u = 0; u < JC; ++u) scr[u * QT] = make_float2(dzv[u], dyzv[u]);
+#pragma unroll 1
                 for (int u = 0; u < JC; ++u) {
-                    const bool pz = dzv[u] < e;
-                    cz[m] += pz ? 1 : 0;
-                    cxz[m] += (pz && dcv[u] < e) ? 1 : 0;
-                    cyz[m] += (dyzv[u] < e) ? 1 : 0;
+                    const float2 sd = scr[u * QT];
+                    float xv[M];
+                    load_members<M>(tx + (c + u) * M, xv);
+#pragma unroll
+                    for (int m = 0; m < M; ++m)
+                        count3(cz[m], cxz[m], cyz[m], sd.x, sd.y,
+                               fabsf(__fsub_rn(xi[m], xv[m])), eps[m]);
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    float dcv[JC];
+                    member_dist<M>(tile, qv, jt, dy, dz, dx, m, c, dcv);
+#pragma unroll
+                    for (int u = 0; u < JC; ++u)
+                        count3(cz[m], cxz[m], cyz[m], dzv[u], dyzv[u], dcv[u], eps[m]);
                 }
             }
         }
+        __syncthreads();
     }
 
     // ---------------- digamma key: exact int64 terms, 128-bit sums ----------------
-    const int lane = tid & 31;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
+        const int nz = (int)cz[m], nxz = (int)cxz[m], nyz = (int)cyz[m];
         long long term = 0;
-        if (qvalid)
-            term = L.q[cz[m] + 1] - L.q[cxz[m] + 1] - L.q[cyz[m] + 1];
+        if (qvalid) term = L.q[nz + 1] - L.q[nxz + 1] - L.q[nyz + 1];
         if (L.dbg_eps && qvalid && s_valid[m] && s_out[m] == L.dbg_out) {
-            L.dbg_eps[i] = eps[m];
-            L.dbg_nxz[i] = cxz[m];
-            L.dbg_nyz[i] = cyz[m];
-            L.dbg_nz[i] = cz[m];
+            L.dbg_eps[ti] = eps[m];
+            L.dbg_nxz[ti] = nxz;
+            L.dbg_nyz[ti] = nyz;
+            L.dbg_nz[ti] = nz;
         }
         // |term| < 2^57 for N < 2^31, so a 32-lane sum fits in int64
 #pragma unroll
@@ -352,6 +562,105 @@ __global__ void fisher_yates_kernel(int32_t *out, long long stride, int n, uint6
     if (in_smem)
         for (int i = threadIdx.x; i < n; i += blockDim.x)
             out[(long long)blockIdx.x * stride + i] = sperm[i];
+}
+
+// ---------------- spatial order: Morton curve over (Y, Z) ----------------
+// One CTA per group: per-dimension ranges, Morton keys (bits interleaved
+// from the most significant, up to 50 bits) packed with the point index, a
+// bitonic sort in shared memory, then the sorted coordinates and the bounding
+// box of every aligned chunk of 8 sorted points.  The order only affects how
+// much work the pruning saves, never a result.
+__global__ void __launch_bounds__(1024) order_kernel(const OrderJob *jobs)
+{
+    extern __shared__ unsigned long long skeys[];
+    __shared__ float s_lo[32], s_hi[32];
+    __shared__ float s_red[2][32];
+    const OrderJob &J = jobs[blockIdx.x];
+    const int N = J.N, D = J.dyz;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nw = blockDim.x >> 5;
+    const float *base = J.base;
+    for (int d = 0; d < D; ++d) {
+        float mn = CUDART_INF_F, mx = -CUDART_INF_F;
+        for (int p = tid; p < N; p += blockDim.x) {
+            const float v = base[J.cols[d] + p];
+            mn = fminf(mn, v);
+            mx = fmaxf(mx, v);
+        }
+        mn = warp_min(mn);
+        mx = warp_max(mx);
+        if (lane == 0) {
+            s_red[0][wid] = mn;
+            s_red[1][wid] = mx;
+        }
+        __syncthreads();
+        if (wid == 0) {
+            mn = lane < nw ? s_red[0][lane] : CUDART_INF_F;
+            mx = lane < nw ? s_red[1][lane] : -CUDART_INF_F;
+            mn = warp_min(mn);
+            mx = warp_max(mx);
+            if (lane == 0) {
+                s_lo[d] = mn;
+                s_hi[d] = mx;
+            }
+        }
+        __syncthreads();
+    }
+    int bits = 50 / D;
+    if (bits > 24) bits = 24;
+    if (bits < 1) bits = 1;
+    const float qmax = (float)((1u << bits) - 1u);
+    int P2 = 1;
+    while (P2 < N) P2 <<= 1;
+    for (int p = tid; p < P2; p += blockDim.x) {
+        unsigned long long key = ~0ull;
+        if (p < N) {
+            unsigned long long mort = 0;
+            unsigned int q[32];
+            for (int d = 0; d < D; ++d) {
+                const float span = s_hi[d] - s_lo[d];
+                float f = span > 0.f ? (base[J.cols[d] + p] - s_lo[d]) / span * qmax : 0.f;
+                f = fminf(fmaxf(f, 0.f), qmax);
+                q[d] = (unsigned int)f;
+            }
+            for (int b = bits - 1; b >= 0; --b)
+                for (int d = 0; d < D; ++d) mort = (mort << 1) | ((q[d] >> b) & 1u);
+            key = (mort << 14) | (unsigned long long)p;
+        }
+        skeys[p] = key;
+    }
+    __syncthreads();
+    for (int kk = 2; kk <= P2; kk <<= 1) {
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int t = tid; t < (P2 >> 1); t += blockDim.x) {
+                const int lo = 2 * jj * (t / jj) + (t % jj);
+                const int hi = lo + jj;
+                const bool up = (lo & kk) == 0;
+                const unsigned long long x = skeys[lo], y = skeys[hi];
+                if ((x > y) == up) {
+                    skeys[lo] = y;
+                    skeys[hi] = x;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int p = tid; p < N; p += blockDim.x) {
+        const int t = (int)(skeys[p] & 0x3FFFull);
+        J.sigma[p] = t;
+        for (int d = 0; d < D; ++d) J.yz[(size_t)d * N + p] = base[J.cols[d] + t];
+    }
+    const int nch = (N + 7) >> 3;
+    for (int e = tid; e < nch * D; e += blockDim.x) {
+        const int d = e / nch, c = e - d * nch;
+        float mn = CUDART_INF_F, mx = -CUDART_INF_F;
+        for (int p = 8 * c; p < min(8 * c + 8, N); ++p) {
+            const float v = base[J.cols[d] + (int)(skeys[p] & 0x3FFFull)];
+            mn = fminf(mn, v);
+            mx = fmaxf(mx, v);
+        }
+        J.box[(size_t)d * nch + c] = make_float2(mn, mx);
+    }
 }
 
 __global__ void finalize_kernel(const unsigned long long *acc, long long *keys, int n_out)
@@ -443,13 +752,6 @@ const void *select_kernel(const KsgVariant &v, bool dx1)
 
 }  // namespace
 
-size_t ksg_smem_bytes(const KsgVariant &v, int dy, int dz, int dx, bool dx1, int jt)
-{
-    const size_t rows_t = (size_t)(dy + dz + v.m * dx);
-    const size_t rows_q = (size_t)(dy + dz + (dx1 ? 0 : v.m * dx));
-    return 4 * (rows_t * (size_t)jt + rows_q * QT);
-}
-
 cudaError_t ksg_prepare_attributes()
 {
     const KsgVariant vs[] = {{4, 4, QT}, {8, 4, QT}, {16, 4, QT}, {2, 0, QT}, {2, 4, QT}};
@@ -461,8 +763,19 @@ cudaError_t ksg_prepare_attributes()
                 cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             if (e != cudaSuccess) return e;
         }
+    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(&order_kernel),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kMaxOrderN * 8);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(reinterpret_cast<const void *>(&stats_kernel),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+cudaError_t launch_order(const OrderJob *jobs, int n_jobs, cudaStream_t st)
+{
+    if (n_jobs <= 0) return cudaSuccess;
+    order_kernel<<<n_jobs, 1024, kMaxOrderN * 8, st>>>(jobs);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ksg(const KsgLaunch &L, const KsgVariant &v, long long n_items, bool dx1,

@@ -189,13 +189,16 @@ te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_para
                     g.y = {ypres};
                     g.z = z;
                     g.dx = (int)xs[0].size();
-                    for (const auto &x : xs) {
-                        const int xfirst = (int)g.xvars.size();
-                        g.xvars.insert(g.xvars.end(), x.begin(), x.end());
-                        for (int s = 0; s <= S; ++s)
+                    // members surrogate-major, so the members a CTA shares carry
+                    // the same permutation; output slots stay candidate-major
+                    const int nx = (int)xs.size();
+                    for (const auto &x : xs) g.xvars.insert(g.xvars.end(), x.begin(), x.end());
+                    for (int s = 0; s <= S; ++s)
+                        for (int c = 0; c < nx; ++c)
                             g.members.push_back(HostMember{
-                                xfirst, s == 0 ? nullptr : pr + (size_t)(s - 1) * N, n_out++});
-                    }
+                                c * g.dx, s == 0 ? nullptr : pr + (size_t)(s - 1) * N,
+                                n_out + c * (S + 1) + s});
+                    n_out += nx * (S + 1);
                     groups.push_back(std::move(g));
                 };
                 t.out_base = n_out;

@@ -267,6 +267,37 @@ te_status run_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_ou
         classes[ClassKey{g.dx == 1, g.k == 4}].push_back(&g);
     }
 
+    // Spatial order for every group without a Theiler window that fits one
+    // sorting CTA: sigma [N], sorted coordinates [dyz][N], chunk boxes.
+    struct OrderOut {
+        size_t sigma, yz, box;
+        int nch;
+    };
+    std::map<const HostGroup *, OrderOut> order_of;
+    std::vector<const HostGroup *> to_order;
+    size_t order_bytes = 0;
+    auto align16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    for (const HostGroup &g : groups) {
+        const int N = g.data->T - g.max_lag;
+        const int dyz = (int)(g.y.size() + g.z.size());
+        if (g.members.empty() || g.theiler != 0 || N > kMaxOrderN || N < 16 || dyz > 32)
+            continue;
+        OrderOut o;
+        o.nch = (N + 7) / 8;
+        o.sigma = order_bytes;
+        order_bytes += align16((size_t)N * 4);
+        o.yz = order_bytes;
+        order_bytes += align16((size_t)dyz * N * 4);
+        o.box = order_bytes;
+        order_bytes += align16((size_t)dyz * o.nch * 8);
+        order_of[&g] = o;
+        to_order.push_back(&g);
+    }
+    if (!to_order.empty()) {
+        if ((st = ensure_dev(ctx, ctx->ws_order, order_bytes))) return st;
+    }
+    char *obase = (char *)ctx->ws_order.p;
+
     // host tables for every class, staged in one pinned block
     struct Plan {
         KsgVariant v;
@@ -313,8 +344,8 @@ te_status run_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_ou
             }
         }
         auto jt_for = [&](size_t budget) {
-            long long room = (long long)budget / 4 - (long long)rows_q * 128;
-            long long jt = room / std::max(rows_t, 1);
+            long long room = (long long)budget - 4LL * rows_q * 128 - 64 - 8 * 8 * 128;
+            long long jt = room / (4LL * rows_t + 8);
             jt &= ~7LL;
             return (int)std::min<long long>(jt, 2048);
         };
@@ -327,7 +358,7 @@ te_status run_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_ou
         p.v = v;
         p.dx1 = dx1;
         p.jt = jt;
-        p.smem = 4 * ((size_t)rows_t * jt + (size_t)rows_q * 128);
+        p.smem = ksg_smem_bytes(rows_t, rows_q, jt, 128);
         p.g_off = gdesc.size();
         p.m_off = mdesc.size();
         p.c_off = cols.size();
@@ -360,6 +391,13 @@ te_status run_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_ou
                 md.out = hm.out;
                 mdesc.push_back(md);
             }
+            auto oit = order_of.find(g);
+            if (oit != order_of.end()) {
+                gd.sigma = (const int *)(obase + oit->second.sigma);
+                gd.yz = (const float *)(obase + oit->second.yz);
+                gd.box = (const float2 *)(obase + oit->second.box);
+                gd.n_chunks8 = oit->second.nch;
+            }
             gd.n_qtiles = (N + 127) / 128;
             gd.n_mblocks = (gd.n_members + v.m - 1) / v.m;
             gd.item_begin = item;
@@ -378,10 +416,27 @@ te_status run_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_ou
         return TE_OK;
     }
 
+    std::vector<OrderJob> ojobs;
+    for (const HostGroup *g : to_order) {
+        const OrderOut &o = order_of[g];
+        OrderJob J{};
+        J.base = g->data->d_series;
+        J.N = g->data->T - g->max_lag;
+        J.dyz = (int)(g->y.size() + g->z.size());
+        int d = 0;
+        for (te_var vv : g->y) J.cols[d++] = vv.proc * g->data->T + g->max_lag - vv.lag;
+        for (te_var vv : g->z) J.cols[d++] = vv.proc * g->data->T + g->max_lag - vv.lag;
+        J.sigma = (int *)(obase + o.sigma);
+        J.yz = (float *)(obase + o.yz);
+        J.box = (float2 *)(obase + o.box);
+        ojobs.push_back(J);
+    }
     const size_t gbytes = gdesc.size() * sizeof(GroupDesc);
     const size_t mbytes = mdesc.size() * sizeof(MemberDesc);
     const size_t cbytes = cols.size() * sizeof(int);
-    if ((st = ensure_pin(ctx, gbytes + mbytes + cbytes + 64))) return st;
+    const size_t obytes = ojobs.size() * sizeof(OrderJob);
+    if ((st = ensure_pin(ctx, gbytes + mbytes + cbytes + obytes + 64))) return st;
+    if ((st = ensure_dev(ctx, ctx->ws_ojobs, obytes + 16))) return st;
     if ((st = ensure_dev(ctx, ctx->ws_groups, gbytes + 16))) return st;
     if ((st = ensure_dev(ctx, ctx->ws_members, mbytes + 16))) return st;
     if ((st = ensure_dev(ctx, ctx->ws_cols, cbytes + 16))) return st;
@@ -392,10 +447,20 @@ te_status run_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_ou
     CK(copy_h2d(ctx, ctx->ws_groups.p, pin, gbytes), "cudaMemcpyAsync");
     CK(copy_h2d(ctx, ctx->ws_members.p, pin + gbytes, mbytes), "cudaMemcpyAsync");
     if (cbytes) CK(copy_h2d(ctx, ctx->ws_cols.p, pin + gbytes + mbytes, cbytes), "cudaMemcpyAsync");
+    if (obytes) {
+        std::memcpy(pin + gbytes + mbytes + cbytes, ojobs.data(), obytes);
+        CK(copy_h2d(ctx, ctx->ws_ojobs.p, pin + gbytes + mbytes + cbytes, obytes),
+           "cudaMemcpyAsync");
+    }
 
     if (!ctx->prepared) {
         CK(ksg_prepare_attributes(), "cudaFuncSetAttribute");
         ctx->prepared = 1;
+    }
+    if (!ojobs.empty()) {
+        CK(launch_order((const OrderJob *)ctx->ws_ojobs.p, (int)ojobs.size(), ctx->stream),
+           "order launch");
+        ctx->stats.launches++;
     }
     CK(cudaEventRecord(ctx->ev_a, ctx->stream), "cudaEventRecord");
     for (const Plan &p : plans) {
@@ -486,8 +551,9 @@ void te_ctx_destroy(te_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    DevBuf *bufs[] = {&ctx->ws_groups, &ctx->ws_members, &ctx->ws_cols, &ctx->ws_acc,
-                      &ctx->ws_keys,   &ctx->ws_perm,    &ctx->ws_stat, &ctx->ws_dbg};
+    DevBuf *bufs[] = {&ctx->ws_groups, &ctx->ws_members, &ctx->ws_cols,  &ctx->ws_acc,
+                      &ctx->ws_keys,   &ctx->ws_perm,    &ctx->ws_stat,  &ctx->ws_dbg,
+                      &ctx->ws_order,  &ctx->ws_ojobs};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->q_dev) cudaFree(ctx->q_dev);
