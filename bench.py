@@ -35,7 +35,6 @@ sys.path.insert(0, ROOT)
 METRIC = "KSG CMI estimates/s incl. surrogates at T=10000"
 UNIT = "estimates/s"
 SM_COUNT = 152
-OPS_PER_MEMBER_PAIR = 10  # kNN pass: sub, max, compare; count pass: sub, 3 compares, 3 adds
 
 
 def _peaks():
@@ -296,8 +295,9 @@ def main():
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     kernel_ms = s1["kernel_ms"] - s0["kernel_ms"]
     pair_evals = s1["pair_evals"] - s0["pair_evals"]
+    pair_evals_bf = s1["pair_evals_bruteforce"] - s0["pair_evals_bruteforce"]
     ksg_launches = s1["ksg_launches"] - s0["ksg_launches"]
-    ops = OPS_PER_MEMBER_PAIR * pair_evals / 2.0
+    ops = s1["ksg_ops"] - s0["ksg_ops"]
     achieved = ops / (kernel_ms / 1e3) / 1e12 if kernel_ms > 0 else None
     peak = SM_COUNT * 128 * sm_max * 1e6 / 1e12
     value = n_est / (ms / 1e3)
@@ -317,7 +317,11 @@ def main():
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
                      "kernel": "ksg_fused_kernel", "kernel_ms_per_launch":
                      kernel_ms / max(ksg_launches, 1), "launches": ksg_launches,
-                     "peak_note": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived)"},
+                     "peak_note": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived)",
+                     "work": "3 ops per executed kNN-pass member-pair, 7 per count-pass one",
+                     "pair_evals_executed": pair_evals, "pair_evals_bruteforce": pair_evals_bf,
+                     "pruned_fraction": (1.0 - pair_evals / pair_evals_bf) if pair_evals_bf
+                     else None},
         "clocks": clk,
     }
     if not args.no_cpu_baseline and world == 1:

@@ -225,12 +225,18 @@ void te_network_result_free(te_network_result *res);
 typedef struct {
     uint64_t estimates;       /* CMI estimates (members) evaluated */
     uint64_t launches;        /* kernel launches issued (all kernels of the library) */
-    uint64_t pair_evals;      /* member x point-pair distance evaluations (both passes) */
+    uint64_t pair_evals;      /* member x point-pair distance evaluations the KSG kernel
+                                 executed (both passes; pairs of skipped chunks excluded) */
     double kernel_ms;         /* summed device time of the KSG kernels (CUDA events on the
                                  context's stream) */
     uint64_t ksg_launches;    /* launches of the fused KSG kernel */
     uint64_t h2d_bytes;       /* bytes copied host -> device by the library */
     uint64_t d2h_bytes;       /* bytes copied device -> host by the library */
+    uint64_t pair_evals_bruteforce; /* member x ordered point pairs x 2 passes: the work of
+                                       the unpruned all-pairs estimator */
+    uint64_t ksg_ops;         /* algorithmic ops of the executed evaluations: 3 per kNN-pass
+                                 pair (subtract, max, compare), 7 per count-pass pair
+                                 (subtract, 3 compares, 3 increments) */
 } te_stats;
 
 te_status te_get_stats(const te_ctx *ctx, te_stats *out);

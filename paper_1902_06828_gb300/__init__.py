@@ -81,7 +81,8 @@ class Context:
         _check(self._h, self._lib.te_get_stats(self._h, C.byref(s)))
         return dict(estimates=s.estimates, launches=s.launches, pair_evals=s.pair_evals,
                     kernel_ms=s.kernel_ms, ksg_launches=s.ksg_launches, h2d_bytes=s.h2d_bytes,
-                    d2h_bytes=s.d2h_bytes)
+                    d2h_bytes=s.d2h_bytes, pair_evals_bruteforce=s.pair_evals_bruteforce,
+                    ksg_ops=s.ksg_ops)
 
     def close(self):
         if getattr(self, "_h", None):

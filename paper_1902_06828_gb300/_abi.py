@@ -61,7 +61,8 @@ class NetworkResult(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("estimates", C.c_uint64), ("launches", C.c_uint64), ("pair_evals", C.c_uint64),
                 ("kernel_ms", C.c_double), ("ksg_launches", C.c_uint64),
-                ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64)]
+                ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
+                ("pair_evals_bruteforce", C.c_uint64), ("ksg_ops", C.c_uint64)]
 
 
 # every symbol include/te_ksg.h declares: name -> (restype, argtypes)

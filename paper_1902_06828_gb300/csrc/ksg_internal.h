@@ -46,8 +46,18 @@ struct OrderJob {
 constexpr int kMaxOrderN = 16384;   // points a CTA can sort in shared memory
 cudaError_t launch_order(const OrderJob *jobs, int n_jobs, cudaStream_t st);
 
+struct ComposeJob {
+    const int *sigma;
+    const int32_t *perm;
+    int32_t *out;
+    int N;
+};
+cudaError_t launch_compose(const ComposeJob *jobs, int n_jobs, int max_n, cudaStream_t st);
+
 struct MemberDesc {
-    const int32_t *perm;    // device permutation of [0, N) applied to X, or nullptr
+    const int32_t *perm;    // device permutation of [0, N) applied to X, or nullptr; in a
+                            // sorted group it is composed with the order (position ->
+                            // time index of X)
     int xcol;               // first index into cols[] of the dx X column offsets
     int out;                // output slot
 };
@@ -65,15 +75,28 @@ struct KsgLaunch {
     int *dbg_nxz, *dbg_nyz, *dbg_nz;
     int dbg_out;
     int jt;                        // points per staged j tile
+    unsigned long long *work;      // [0] += member-pair evaluations executed (both passes),
+                                   // [1] += algorithmic ops of those evaluations
 };
 
 // Kernel variants: members per thread and k.  kgen = 0 means k is a template
 // constant; otherwise a runtime k <= TE_MAX_K.
 struct KsgVariant {
-    int m;      // members per thread
+    int m;      // members per thread; 32 selects the member-lane kernel
     int kt;     // template k (0 = runtime k)
-    int qt;     // query points per CTA (threads)
+    int qt;     // threads per CTA
 };
+
+// member-lane kernel (single-variable X): 32 members x 32 query points per CTA
+constexpr int kLaneQueries = 32;
+constexpr int kLaneThreads = 256;
+inline size_t ksg_lane_smem_bytes(int dyz, int jt)
+{
+    const int warps = kLaneThreads / 32;
+    return 4 * ((size_t)dyz * jt + 32 * (size_t)(jt + 4)) +
+           (size_t)warps * (2 * 4 * 8 * 4 + 4 * 4 * (size_t)dyz + 4 * (size_t)(jt / 64)) + 8 +
+           8 * (size_t)dyz * (jt / 8);
+}
 
 cudaError_t launch_ksg(const KsgLaunch &L, const KsgVariant &v, long long n_items, bool dx1,
                        size_t smem_bytes, cudaStream_t st);

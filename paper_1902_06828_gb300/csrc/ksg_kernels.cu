@@ -230,7 +230,9 @@ __global__ void __launch_bounds__(QT) ksg_fused_kernel(const KsgLaunch L)
     for (int m = 0; m < M; ++m) {
         const int mi = min(mb * M + m, G.n_members - 1);
         const MemberDesc md = L.members[G.member_begin + mi];
-        const int pi = md.perm ? md.perm[ti] : ti;
+        // member permutations of sorted groups are composed with the order:
+        // they map a position straight to the time index of X
+        const int pi = md.perm ? md.perm[ic] : ti;
         if (DX1) {
             xi[m] = base[L.cols[md.xcol] + pi];
         } else {
@@ -257,10 +259,7 @@ __global__ void __launch_bounds__(QT) ksg_fused_kernel(const KsgLaunch L)
             for (int jj = tid; jj < jt; jj += QT) {
                 const int j = j0 + jj;
                 int t = 0;
-                if (j < N) {
-                    t = sorted ? G.sigma[j] : j;
-                    if (shared_perm && perm0) t = perm0[t];
-                }
+                if (j < N) t = (shared_perm && perm0) ? perm0[j] : (sorted ? G.sigma[j] : j);
                 sidx[jj] = t;
             }
         }
@@ -279,9 +278,8 @@ __global__ void __launch_bounds__(QT) ksg_fused_kernel(const KsgLaunch L)
                 const int j = j0 + jj;
                 float v = 0.f;
                 if (j < N) {
-                    int t = use_idx ? sidx[jj] : j;
                     const int32_t *perm = shared_perm ? nullptr : s_perm[m];
-                    if (perm) t = perm[t];
+                    const int t = perm ? perm[j] : (use_idx ? sidx[jj] : j);
                     v = base[s_xoff[m] + t];
                 }
                 tx[e] = v;
@@ -296,8 +294,7 @@ __global__ void __launch_bounds__(QT) ksg_fused_kernel(const KsgLaunch L)
                     const int j = j0 + jj;
                     float v = 0.f;
                     if (j < N) {
-                        int t = use_idx ? sidx[jj] : j;
-                        if (perm) t = perm[t];
+                        const int t = perm ? perm[j] : (use_idx ? sidx[jj] : j);
                         v = base[off + t];
                     }
                     tile[r * jt + jj] = v;
@@ -359,6 +356,7 @@ __global__ void __launch_bounds__(QT) ksg_fused_kernel(const KsgLaunch L)
         thr[m] = CUDART_INF_F;
     }
     float tmax_w = CUDART_INF_F;   // max over the warp's lanes and members of thr
+    unsigned int executed1 = 0, executed2 = 0;   // 8-point chunks this warp evaluated
     {
         // sorted mode: start at this CTA's own tile and spiral outwards
         const int home = sorted ? min(qlo / jt, ntiles - 1) : 0;
@@ -387,6 +385,7 @@ __global__ void __launch_bounds__(QT) ksg_fused_kernel(const KsgLaunch L)
             __syncthreads();
             for (int c = 0; c < jn; c += JC) {
                 if (sorted && wlb[warp * cpt + (c >> 3)].x >= tmax_w) continue;
+                ++executed1;
                 float dzv[JC], dyzv[JC];
                 shared_dist(tile, qv, jt, dy, dz, c, dzv, dyzv);
                 if (needs_mask(j0 + c)) apply_mask(j0 + c, dzv, dyzv);
@@ -468,6 +467,7 @@ __global__ void __launch_bounds__(QT) ksg_fused_kernel(const KsgLaunch L)
         __syncthreads();
         for (int c = 0; c < jn; c += JC) {
             if (prune2 && wlb[warp * cpt + (c >> 3)].y >= emax_w) continue;
+            ++executed2;
             float dzv[JC], dyzv[JC];
             shared_dist(tile, qv, jt, dy, dz, c, dzv, dyzv);
             if (needs_mask(j0 + c)) apply_mask(j0 + c, dzv, dyzv);
@@ -500,6 +500,19 @@ __global__ void __launch_bounds__(QT) ksg_fused_kernel(const KsgLaunch L)
         __syncthreads();
     }
 
+    if (L.work) {
+        const unsigned lanes = __popc(__ballot_sync(0xffffffffu, qvalid));
+        if (lane == 0) {
+            int mv = 0;
+#pragma unroll
+            for (int m = 0; m < M; ++m) mv += s_valid[m];
+            const unsigned long long per = (unsigned long long)JC * lanes * (unsigned)mv;
+            // evaluations, and algorithmic ops: 3 per kNN-pass and 7 per count-pass pair
+            atomicAdd(&L.work[0], (unsigned long long)(executed1 + executed2) * per);
+            atomicAdd(&L.work[1], (3ull * executed1 + 7ull * executed2) * per);
+        }
+    }
+
     // ---------------- digamma key: exact int64 terms, 128-bit sums ----------------
 #pragma unroll
     for (int m = 0; m < M; ++m) {
@@ -520,6 +533,409 @@ __global__ void __launch_bounds__(QT) ksg_fused_kernel(const KsgLaunch L)
             const long long hi = term >> 32;
             atomicAdd(&L.acc[2 * s_out[m]], lo);
             atomicAdd(&L.acc[2 * s_out[m] + 1], (unsigned long long)hi);
+        }
+    }
+}
+
+// ---------------- member-lane kernel ----------------
+// ksg_lane_kernel -- for single-variable X (every candidate of the greedy
+// steps).  Lanes are members: a CTA owns 32 members (one per lane) and 32
+// query points, 4 per warp.  Every prune decision is taken per query point
+// (a warp-uniform branch), against the maximum over the 32 members of that
+// point's current k-th distance (pass 1) or eps (pass 2), so the bounds are
+// as tight as a single point allows.  d_Z and d_YZ of a chunk are computed
+// lane-parallel over (query, point) pairs and read back as broadcasts; the X
+// values of a lane's member come from a padded [member][point] tile.
+constexpr int LQ = 4;            // query points per warp
+constexpr int LW = 8;            // warps per CTA
+constexpr int LQC = LQ * LW;     // query points per CTA
+constexpr int kMaxLaneChunks = 64;   // chunks of 8 per staged tile (tile <= 512 points)
+
+template <int KT>
+__global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const KsgLaunch L)
+{
+    constexpr int KB = KT > 0 ? KT : KMAX;
+    extern __shared__ __align__(16) float smem[];
+
+    const long long item = blockIdx.x;
+    int glo = 0, ghi = L.n_groups - 1;
+    while (glo < ghi) {
+        const int mid = (glo + ghi + 1) >> 1;
+        if (L.groups[mid].item_begin <= item) glo = mid;
+        else ghi = mid - 1;
+    }
+    const GroupDesc G = L.groups[glo];
+    const long long local = item - G.item_begin;
+    const int mb = (int)(local / G.n_qtiles);
+    const int qtile = (int)(local % G.n_qtiles);
+    const int N = G.N, dy = G.dy, dz = G.dz, w = G.theiler;
+    const int dyz = dy + dz;
+    const int k = KT > 0 ? KT : G.k;
+    const int jt = L.jt, jtp = jt + 4, cpt = jt >> 3, wpt = cpt >> 3;
+    const float *__restrict__ base = G.base;
+    const bool sorted = G.sigma != nullptr;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float *t_yz = smem;                                   // [dyz][jt]
+    float *t_x = t_yz + dyz * jt;                         // [32][jtp]
+    float *s_dz = t_x + 32 * jtp;                         // [LW][LQ][8]
+    float *s_dyz = s_dz + LW * LQ * 8;                    // [LW][LQ][8]
+    float *s_q = s_dyz + LW * LQ * 8;                     // [LW][LQ][dyz]
+    unsigned *s_bits = reinterpret_cast<unsigned *>(s_q + LW * LQ * dyz);  // [LW][wpt]
+    float2 *s_box = reinterpret_cast<float2 *>(
+        (reinterpret_cast<uintptr_t>(s_bits + LW * wpt) + 7) & ~(uintptr_t)7);  // [dyz][cpt]
+    __shared__ const int32_t *s_mperm[32];
+    __shared__ int s_mxoff[32];
+    __shared__ int s_shared_perm;
+    __shared__ int s_live[2][LW];
+    __shared__ float s_bound[LW][LQ];
+    __shared__ long long s_red[LW][32];
+    __shared__ int s_clist[kMaxLaneChunks];   // live chunks of the current tile
+    __shared__ int s_nlive;
+
+    // ---- this lane's member ----
+    const int mi = mb * 32 + lane;
+    const bool mvalid = mi < G.n_members;
+    const MemberDesc md = L.members[G.member_begin + min(mi, G.n_members - 1)];
+    const int32_t *perm = md.perm;
+    const int xoff = L.cols[md.xcol];
+    if (warp == 0) {
+        s_mperm[lane] = perm;
+        s_mxoff[lane] = xoff;
+        const unsigned long long p0 =
+            __shfl_sync(0xffffffffu, (unsigned long long)(uintptr_t)perm, 0);
+        const int same = __all_sync(0xffffffffu, (unsigned long long)(uintptr_t)perm == p0);
+        if (lane == 0) s_shared_perm = same;
+    }
+
+    auto yz_off = [&](int d) {
+        return d < dy ? L.cols[G.ycol + d] : L.cols[G.zcol + d - dy];
+    };
+    const int qbase = qtile * LQC + warp * LQ;   // first query position of this warp
+
+    // ---- the warp's query points ----
+    float xi[LQ];
+#pragma unroll
+    for (int a = 0; a < LQ; ++a) {
+        const int qc = min(qbase + a, N - 1);
+        xi[a] = base[xoff + (perm ? perm[qc] : (sorted ? G.sigma[qc] : qc))];
+    }
+    for (int e = lane; e < LQ * dyz; e += 32) {
+        const int a = e / dyz, d = e - a * dyz;
+        const int qc = min(qbase + a, N - 1);
+        s_q[(warp * LQ + a) * dyz + d] = sorted ? G.yz[(size_t)d * N + qc] : base[yz_off(d) + qc];
+    }
+    if (lane < LQ) s_bound[warp][lane] = CUDART_INF_F;
+    __syncthreads();
+    const bool shared_perm = s_shared_perm != 0;
+    const int32_t *perm0 = s_mperm[0];
+
+    // CTA-wide list of the tile's chunks that are live for some warp; every
+    // warp has written its bits before the barrier that precedes this call
+    auto build_list = [&]() {
+        if (warp == 0) {
+            int n = 0;
+            for (int c0 = 0; c0 < cpt; c0 += 32) {
+                const int c = c0 + lane;
+                unsigned any = 0;
+                if (c < cpt)
+                    for (int b = 0; b < LW; ++b)
+                        any |= (s_bits[b * wpt + (c >> 3)] >> (4 * (c & 7))) & 0xFu;
+                const unsigned mask = __ballot_sync(0xffffffffu, any != 0);
+                if (any) s_clist[n + __popc(mask & ((1u << lane) - 1u))] = c;
+                n += __popc(mask);
+            }
+            if (lane == 0) s_nlive = n;
+        }
+        __syncthreads();
+    };
+
+    // stage the live chunks: thread = (member m, point u) for X, (dim, point)
+    // for Y and Z; four chunks per round keep several gathers in flight
+    auto stage = [&](int j0) {
+        const int nl = s_nlive;
+        const int m = tid >> 3, u = tid & 7;
+        const int32_t *pm = shared_perm ? perm0 : s_mperm[m];
+        const int xo = s_mxoff[m];
+        for (int r0 = 0; r0 < nl; r0 += 4) {
+            float xv4[4], yz4[4];
+            int cc[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                cc[q] = r0 + q < nl ? s_clist[r0 + q] : -1;
+                xv4[q] = 0.f;
+                yz4[q] = 0.f;
+                if (cc[q] >= 0) {
+                    const int j = j0 + cc[q] * 8 + u;
+                    if (j < N) {
+                        const int t = pm ? pm[j] : (sorted ? G.sigma[j] : j);
+                        xv4[q] = base[xo + t];
+                        if (tid < dyz * 8) {
+                            const int d = tid >> 3;
+                            yz4[q] = sorted ? G.yz[(size_t)d * N + j] : base[yz_off(d) + j];
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (cc[q] < 0) continue;
+                t_x[m * jtp + cc[q] * 8 + u] = xv4[q];
+                if (tid < dyz * 8) t_yz[(tid >> 3) * jt + cc[q] * 8 + u] = yz4[q];
+            }
+        }
+    };
+
+    // the tile's chunk boxes, loaded once per CTA (sorted mode); callers
+    // synchronise before tile_live reads them
+    auto load_boxes = [&](int j0, int jn) {
+        const int nct = (jn + 7) >> 3;
+        for (int e = tid; e < dyz * nct; e += LW * 32) {
+            const int d = e / nct, c = e - d * nct;
+            s_box[d * cpt + c] = G.box[(size_t)d * G.n_chunks8 + (j0 >> 3) + c];
+        }
+    };
+
+    // liveness of every (query, chunk) of the tile for this warp: bit 4c'+a of
+    // word c/8; a lower bound (exact in float, rounding is monotone) on d_YZ
+    // (pass 1) or d_Z (pass 2) below the query's bound keeps the chunk
+    auto tile_live = [&](int j0, int jn, bool pass1) {
+        const int nct = (jn + 7) >> 3;
+        bool any = false;
+        for (int wb = 0; wb < wpt; ++wb) {
+            const int c = wb * 8 + (lane >> 2), a = lane & 3;
+            bool live = false;
+            if (c < nct) {
+                if (!sorted) {
+                    live = true;
+                } else {
+                    const float *qc = s_q + (warp * LQ + a) * dyz;
+                    float lb = 0.f;
+                    for (int d = pass1 ? 0 : dy; d < dyz; ++d) {
+                        const float2 b = s_box[d * cpt + c];
+                        const float q = qc[d];
+                        lb = fmaxf(lb, fmaxf(fmaxf(__fsub_rn(b.x, q), __fsub_rn(q, b.y)), 0.f));
+                    }
+                    live = lb < s_bound[warp][a];
+                }
+            }
+            const unsigned word = __ballot_sync(0xffffffffu, live);
+            if (lane == 0) s_bits[warp * wpt + wb] = word;
+            any |= word != 0;
+        }
+        __syncwarp();
+        return any;
+    };
+
+    // d_Z and d_YZ of the live queries against the 8 points of the chunk at c;
+    // lane = (query a, point u); masked pairs (past N, self, Theiler band) = +inf
+    auto chunk_dist = [&](int j0, int c, unsigned live4) {
+        const int a = lane >> 3, u = lane & 7;
+        float dzv = -CUDART_INF_F, dyzv = -CUDART_INF_F;
+        if ((live4 >> a) & 1u) {
+            const float *qc = s_q + (warp * LQ + a) * dyz;
+            for (int d = dy; d < dyz; ++d)
+                dzv = fmaxf(dzv, fabsf(__fsub_rn(qc[d], t_yz[d * jt + c + u])));
+            dyzv = dzv;
+            for (int d = 0; d < dy; ++d)
+                dyzv = fmaxf(dyzv, fabsf(__fsub_rn(qc[d], t_yz[d * jt + c + u])));
+            const int j = j0 + c + u;
+            const int qp = min(qbase + a, N - 1);
+            const int gap = j > qp ? j - qp : qp - j;
+            if (j >= N || gap <= w) {
+                dzv = CUDART_INF_F;
+                dyzv = CUDART_INF_F;
+            }
+        }
+        s_dz[(warp * LQ + a) * 8 + u] = dzv;
+        s_dyz[(warp * LQ + a) * 8 + u] = dyzv;
+        __syncwarp();
+    };
+
+    const int ntiles = (N + jt - 1) / jt;
+    unsigned executed1 = 0, executed2 = 0;
+
+    // ---------------- pass 1: k nearest joint distances ----------------
+    float buf[LQ][KB];
+    float thr[LQ];
+#pragma unroll
+    for (int a = 0; a < LQ; ++a) {
+#pragma unroll
+        for (int b = 0; b < KB; ++b) buf[a][b] = CUDART_INF_F;
+        thr[a] = CUDART_INF_F;
+    }
+    {
+        const int home = sorted ? min((qtile * LQC) / jt, ntiles - 1) : 0;
+        int up = home + 1, down = home - 1;
+        bool toggle = true;
+        for (int s = 0; s < ntiles; ++s) {
+            int t;
+            if (s == 0) t = home;
+            else if ((toggle && up < ntiles) || down < 0) t = up++;
+            else t = down--;
+            toggle = !toggle;
+            const int j0 = t * jt;
+            const int jn = min(jt, N - j0);
+            if (sorted) {
+                load_boxes(j0, jn);
+                __syncthreads();
+            }
+            const bool live = tile_live(j0, jn, true);
+            if (lane == 0) s_live[s & 1][warp] = live;
+            __syncthreads();
+            int any = 0;
+#pragma unroll
+            for (int b = 0; b < LW; ++b) any |= s_live[s & 1][b];
+            if (!any) continue;
+            build_list();
+            stage(j0);
+            __syncthreads();
+            const int nl = s_nlive;
+            for (int li = 0; li < nl; ++li) {
+                const int c = s_clist[li] * JC;
+                const unsigned live4 = (s_bits[warp * wpt + (c >> 6)] >> (4 * ((c >> 3) & 7))) & 0xFu;
+                if (!live4) continue;
+                chunk_dist(j0, c, live4);
+                float xv[JC];
+                load8(t_x + lane * jtp + c, xv);
+#pragma unroll
+                for (int a = 0; a < LQ; ++a) {
+                    if (!((live4 >> a) & 1u)) continue;
+                    ++executed1;
+                    float dv[JC];
+                    load8(s_dyz + (warp * LQ + a) * 8, dv);
+                    float D[JC];
+#pragma unroll
+                    for (int u = 0; u < JC; ++u) D[u] = fmaxf(fabsf(__fsub_rn(xi[a], xv[u])), dv[u]);
+                    // one test for the 8 points; the insertions are the rare path
+                    const float mn = fminf(fminf(fminf(D[0], D[1]), fminf(D[2], D[3])),
+                                           fminf(fminf(D[4], D[5]), fminf(D[6], D[7])));
+                    if (mn < thr[a]) {
+#pragma unroll
+                        for (int u = 0; u < JC; ++u) {
+                            if (D[u] < thr[a]) {
+                                topk_insert<KB>(buf[a], D[u]);
+                                thr[a] = KT > 0 ? buf[a][KB - 1] : topk_at<KB>(buf[a], k - 1);
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            if (sorted) {
+#pragma unroll
+                for (int a = 0; a < LQ; ++a) {
+                    const float tm = warp_max(thr[a]);
+                    if (lane == 0) s_bound[warp][a] = tm;
+                }
+                __syncwarp();
+            }
+            __syncthreads();
+        }
+    }
+
+    // ---------------- pass 2: strict range counts ----------------
+    float eps[LQ], cz[LQ], cxz[LQ], cyz[LQ];
+#pragma unroll
+    for (int a = 0; a < LQ; ++a) {
+        eps[a] = thr[a];
+        cz[a] = cxz[a] = cyz[a] = 0.f;
+    }
+    const bool prune2 = sorted && dz > 0;   // with empty Z every j counts in n_xz
+#pragma unroll
+    for (int a = 0; a < LQ; ++a) {
+        const float em = warp_max(eps[a]);
+        if (lane == 0) s_bound[warp][a] = prune2 ? em : CUDART_INF_F;
+    }
+    __syncwarp();
+    for (int t = 0; t < ntiles; ++t) {
+        const int j0 = t * jt;
+        const int jn = min(jt, N - j0);
+        bool live = true;
+        if (prune2) {
+            load_boxes(j0, jn);
+            __syncthreads();
+            live = tile_live(j0, jn, false);
+        }
+        else {
+            // no pruning: every chunk below the end of the data is live
+            const int nct = (jn + 7) >> 3;
+            for (int wb = lane; wb < wpt; wb += 32) {
+                const int lo = wb * 8;
+                const int n = nct - lo >= 8 ? 8 : (nct - lo > 0 ? nct - lo : 0);
+                s_bits[warp * wpt + wb] = n >= 8 ? 0xffffffffu : ((1u << (4 * n)) - 1u);
+            }
+            __syncwarp();
+        }
+        if (lane == 0) s_live[t & 1][warp] = live;
+        __syncthreads();
+        int any = 0;
+#pragma unroll
+        for (int b = 0; b < LW; ++b) any |= s_live[t & 1][b];
+        if (!any) continue;
+        build_list();
+        stage(j0);
+        __syncthreads();
+        const int nl = s_nlive;
+        for (int li = 0; li < nl; ++li) {
+            const int c = s_clist[li] * JC;
+            const unsigned live4 = (s_bits[warp * wpt + (c >> 6)] >> (4 * ((c >> 3) & 7))) & 0xFu;
+            if (!live4) continue;
+            chunk_dist(j0, c, live4);
+            float xv[JC];
+            load8(t_x + lane * jtp + c, xv);
+#pragma unroll
+            for (int a = 0; a < LQ; ++a) {
+                if (!((live4 >> a) & 1u)) continue;
+                ++executed2;
+                float zv[JC], yv[JC];
+                load8(s_dz + (warp * LQ + a) * 8, zv);
+                load8(s_dyz + (warp * LQ + a) * 8, yv);
+#pragma unroll
+                for (int u = 0; u < JC; ++u)
+                    count3(cz[a], cxz[a], cyz[a], zv[u], yv[u], fabsf(__fsub_rn(xi[a], xv[u])),
+                           eps[a]);
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+
+    // ---------------- work counters, digamma key ----------------
+    if (L.work) {
+        const unsigned mv = __popc(__ballot_sync(0xffffffffu, mvalid));
+        if (lane == 0) {
+            const unsigned long long per = (unsigned long long)JC * mv;
+            atomicAdd(&L.work[0], (unsigned long long)(executed1 + executed2) * per);
+            atomicAdd(&L.work[1], (3ull * executed1 + 7ull * executed2) * per);
+        }
+    }
+    long long term = 0;
+#pragma unroll
+    for (int a = 0; a < LQ; ++a) {
+        const int nz = (int)cz[a], nxz = (int)cxz[a], nyz = (int)cyz[a];
+        if (qbase + a < N) {
+            term += L.q[nz + 1] - L.q[nxz + 1] - L.q[nyz + 1];
+            if (L.dbg_eps && mvalid && md.out == L.dbg_out) {
+                const int tq = sorted ? G.sigma[qbase + a] : qbase + a;
+                L.dbg_eps[tq] = eps[a];
+                L.dbg_nxz[tq] = nxz;
+                L.dbg_nyz[tq] = nyz;
+                L.dbg_nz[tq] = nz;
+            }
+        }
+    }
+    s_red[warp][lane] = term;
+    __syncthreads();
+    if (warp == 0) {
+        long long sum = 0;
+#pragma unroll
+        for (int b = 0; b < LW; ++b) sum += s_red[b][lane];   // |sum| < 32 * 2^57
+        if (mvalid) {
+            const unsigned long long lo = (unsigned long long)sum & 0xffffffffull;
+            const long long hi = sum >> 32;
+            atomicAdd(&L.acc[2 * md.out], lo);
+            atomicAdd(&L.acc[2 * md.out + 1], (unsigned long long)hi);
         }
     }
 }
@@ -663,6 +1079,15 @@ __global__ void __launch_bounds__(1024) order_kernel(const OrderJob *jobs)
     }
 }
 
+// out[p] = perm[sigma[p]]: a surrogate permutation composed with a group's
+// spatial order (index arrays only; the data is never copied)
+__global__ void compose_kernel(const ComposeJob *jobs)
+{
+    const ComposeJob J = jobs[blockIdx.y];
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < J.N; p += gridDim.x * blockDim.x)
+        J.out[p] = J.perm[J.sigma[p]];
+}
+
 __global__ void finalize_kernel(const unsigned long long *acc, long long *keys, int n_out)
 {
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
@@ -731,6 +1156,11 @@ const void *kptr()
 
 const void *select_kernel(const KsgVariant &v, bool dx1)
 {
+    if (dx1 && v.m == 32) {
+        if (v.kt == 4) return reinterpret_cast<const void *>(&ksg_lane_kernel<4>);
+        if (v.kt == 0) return reinterpret_cast<const void *>(&ksg_lane_kernel<0>);
+        return nullptr;
+    }
     if (dx1) {
         if (v.kt == 4) {
             if (v.m == 4) return kptr<4, 4, true>();
@@ -754,7 +1184,8 @@ const void *select_kernel(const KsgVariant &v, bool dx1)
 
 cudaError_t ksg_prepare_attributes()
 {
-    const KsgVariant vs[] = {{4, 4, QT}, {8, 4, QT}, {16, 4, QT}, {2, 0, QT}, {2, 4, QT}};
+    const KsgVariant vs[] = {{4, 4, QT},  {8, 4, QT},  {16, 4, QT}, {2, 0, QT},
+                             {2, 4, QT},  {32, 4, LW * 32}, {32, 0, LW * 32}};
     for (const auto &v : vs)
         for (int d = 0; d < 2; ++d) {
             const void *f = select_kernel(v, d == 0);
@@ -769,6 +1200,14 @@ cudaError_t ksg_prepare_attributes()
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(reinterpret_cast<const void *>(&stats_kernel),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+cudaError_t launch_compose(const ComposeJob *jobs, int n_jobs, int max_n, cudaStream_t st)
+{
+    if (n_jobs <= 0) return cudaSuccess;
+    const int bx = (max_n + 255) / 256 < 64 ? (max_n + 255) / 256 : 64;
+    compose_kernel<<<dim3(bx, n_jobs), 256, 0, st>>>(jobs);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_order(const OrderJob *jobs, int n_jobs, cudaStream_t st)
@@ -787,7 +1226,7 @@ cudaError_t launch_ksg(const KsgLaunch &L, const KsgVariant &v, long long n_item
     if (n_items > 0x7fffffffLL) return cudaErrorInvalidValue;
     KsgLaunch arg = L;
     void *args[] = {&arg};
-    return cudaLaunchKernel(f, dim3((unsigned)n_items), dim3(QT), args, smem_bytes, st);
+    return cudaLaunchKernel(f, dim3((unsigned)n_items), dim3(v.qt), args, smem_bytes, st);
 }
 
 cudaError_t launch_perms(int32_t *out, long long stride, int n, uint64_t seed, uint64_t target,

@@ -225,8 +225,6 @@ te_status validate_estimate(te_ctx *ctx, const te_data *data, const te_var *x, i
 // ---- engine ----------------------------------------------------------------
 namespace {
 
-constexpr int kSMs = 152;
-
 struct ClassKey {
     bool dx1;
     bool k4;
@@ -235,18 +233,6 @@ struct ClassKey {
         return std::tie(dx1, k4) < std::tie(o.dx1, o.k4);
     }
 };
-
-long long count_ctas(const std::vector<const HostGroup *> &gs, int M)
-{
-    long long n = 0;
-    for (const HostGroup *g : gs) {
-        const long long N = g->data->T - g->max_lag;
-        const long long qt = (N + 127) / 128;
-        const long long mb = ((long long)g->members.size() + M - 1) / M;
-        n += qt * mb;
-    }
-    return n;
-}
 
 }  // namespace
 
@@ -298,6 +284,25 @@ te_status run_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_ou
     }
     char *obase = (char *)ctx->ws_order.p;
 
+    // every surrogate permutation of a sorted group is composed with the
+    // group's order, so kernels index X by position with one load
+    std::map<std::pair<const HostGroup *, const int32_t *>, size_t> cperm_of;
+    size_t cperm_elems = 0;
+    for (const HostGroup *g : to_order) {
+        const int N = g->data->T - g->max_lag;
+        for (const HostMember &hm : g->members) {
+            if (!hm.perm) continue;
+            auto key = std::make_pair(g, hm.perm);
+            if (cperm_of.count(key)) continue;
+            cperm_of[key] = cperm_elems;
+            cperm_elems += ((size_t)N + 3) & ~(size_t)3;
+        }
+    }
+    if (cperm_elems) {
+        if ((st = ensure_dev(ctx, ctx->ws_cperm, cperm_elems * 4))) return st;
+    }
+    int32_t *cbase = (int32_t *)ctx->ws_cperm.p;
+
     // host tables for every class, staged in one pinned block
     struct Plan {
         KsgVariant v;
@@ -318,15 +323,15 @@ te_status run_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_ou
         const bool dx1 = kv.first.dx1, k4 = kv.first.k4;
         auto &gs = kv.second;
         KsgVariant v{4, 4, 128};
-        if (!k4) {
+        if (dx1) {
+            v = KsgVariant{32, k4 ? 4 : 0, kLaneThreads};   // member-lane kernel
+        } else if (!k4) {
             v = KsgVariant{2, 0, 128};
-        } else if (dx1) {
-            v.m = 16;
-            if (count_ctas(gs, 16) < 4LL * kSMs) v.m = 8;
-            if (v.m == 8 && count_ctas(gs, 8) < 4LL * kSMs) v.m = 4;
         } else {
             v.m = 4;
         }
+        const bool lanek = v.m == 32;
+        const int qsz = lanek ? kLaneQueries : 128;
         int rows_t = 0, rows_q = 0, maxN = 0;
         for (const HostGroup *g : gs) {
             const int dyz = (int)g->y.size() + (int)g->z.size();
@@ -349,16 +354,28 @@ te_status run_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_ou
             jt &= ~7LL;
             return (int)std::min<long long>(jt, 2048);
         };
-        int jt = jt_for(40 * 1024);
-        if (jt < 64) jt = jt_for(190 * 1024);
-        if (jt < 8) return fail(ctx, TE_EINTERNAL, "shared-memory tile does not fit");
-        jt = std::min(jt, (maxN + 7) & ~7);
+        int jt;
+        size_t smem;
+        if (lanek) {
+            int maxdyz = 0;
+            for (const HostGroup *g : gs)
+                maxdyz = std::max(maxdyz, (int)(g->y.size() + g->z.size()));
+            jt = 256;
+            if (maxN < jt) jt = std::max(64, (maxN + 63) & ~63);
+            smem = ksg_lane_smem_bytes(maxdyz, jt);
+        } else {
+            jt = jt_for(40 * 1024);
+            if (jt < 64) jt = jt_for(190 * 1024);
+            if (jt < 8) return fail(ctx, TE_EINTERNAL, "shared-memory tile does not fit");
+            jt = std::min(jt, (maxN + 7) & ~7);
+            smem = ksg_smem_bytes(rows_t, rows_q, jt, 128);
+        }
 
         Plan p;
         p.v = v;
         p.dx1 = dx1;
         p.jt = jt;
-        p.smem = ksg_smem_bytes(rows_t, rows_q, jt, 128);
+        p.smem = smem;
         p.g_off = gdesc.size();
         p.m_off = mdesc.size();
         p.c_off = cols.size();
@@ -384,9 +401,11 @@ te_status run_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_ou
             for (te_var vv : g->xvars) cols.push_back(off(vv));
             gd.member_begin = (int)(mdesc.size() - p.m_off);
             gd.n_members = (int)g->members.size();
+            const bool grp_sorted = order_of.count(g) != 0;
             for (const HostMember &hm : g->members) {
                 MemberDesc md;
                 md.perm = hm.perm;
+                if (grp_sorted && hm.perm) md.perm = cbase + cperm_of[std::make_pair(g, hm.perm)];
                 md.xcol = xbase + hm.xcol_first;
                 md.out = hm.out;
                 mdesc.push_back(md);
@@ -398,7 +417,7 @@ te_status run_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_ou
                 gd.box = (const float2 *)(obase + oit->second.box);
                 gd.n_chunks8 = oit->second.nch;
             }
-            gd.n_qtiles = (N + 127) / 128;
+            gd.n_qtiles = (N + qsz - 1) / qsz;
             gd.n_mblocks = (gd.n_members + v.m - 1) / v.m;
             gd.item_begin = item;
             item += (long long)gd.n_qtiles * gd.n_mblocks;
@@ -431,12 +450,25 @@ te_status run_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_ou
         J.box = (float2 *)(obase + o.box);
         ojobs.push_back(J);
     }
+    std::vector<ComposeJob> cjobs;
+    int max_cn = 0;
+    for (auto &kv : cperm_of) {
+        const HostGroup *g = kv.first.first;
+        ComposeJob J;
+        J.sigma = (const int *)(obase + order_of[g].sigma);
+        J.perm = kv.first.second;
+        J.out = cbase + kv.second;
+        J.N = g->data->T - g->max_lag;
+        max_cn = std::max(max_cn, J.N);
+        cjobs.push_back(J);
+    }
     const size_t gbytes = gdesc.size() * sizeof(GroupDesc);
     const size_t mbytes = mdesc.size() * sizeof(MemberDesc);
     const size_t cbytes = cols.size() * sizeof(int);
     const size_t obytes = ojobs.size() * sizeof(OrderJob);
-    if ((st = ensure_pin(ctx, gbytes + mbytes + cbytes + obytes + 64))) return st;
-    if ((st = ensure_dev(ctx, ctx->ws_ojobs, obytes + 16))) return st;
+    const size_t jbytes = cjobs.size() * sizeof(ComposeJob);
+    if ((st = ensure_pin(ctx, gbytes + mbytes + cbytes + obytes + jbytes + 64))) return st;
+    if ((st = ensure_dev(ctx, ctx->ws_ojobs, obytes + jbytes + 16))) return st;
     if ((st = ensure_dev(ctx, ctx->ws_groups, gbytes + 16))) return st;
     if ((st = ensure_dev(ctx, ctx->ws_members, mbytes + 16))) return st;
     if ((st = ensure_dev(ctx, ctx->ws_cols, cbytes + 16))) return st;
@@ -447,9 +479,10 @@ te_status run_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_ou
     CK(copy_h2d(ctx, ctx->ws_groups.p, pin, gbytes), "cudaMemcpyAsync");
     CK(copy_h2d(ctx, ctx->ws_members.p, pin + gbytes, mbytes), "cudaMemcpyAsync");
     if (cbytes) CK(copy_h2d(ctx, ctx->ws_cols.p, pin + gbytes + mbytes, cbytes), "cudaMemcpyAsync");
-    if (obytes) {
+    if (obytes + jbytes) {
         std::memcpy(pin + gbytes + mbytes + cbytes, ojobs.data(), obytes);
-        CK(copy_h2d(ctx, ctx->ws_ojobs.p, pin + gbytes + mbytes + cbytes, obytes),
+        std::memcpy(pin + gbytes + mbytes + cbytes + obytes, cjobs.data(), jbytes);
+        CK(copy_h2d(ctx, ctx->ws_ojobs.p, pin + gbytes + mbytes + cbytes, obytes + jbytes),
            "cudaMemcpyAsync");
     }
 
@@ -462,6 +495,14 @@ te_status run_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_ou
            "order launch");
         ctx->stats.launches++;
     }
+    if (!cjobs.empty()) {
+        CK(launch_compose((const ComposeJob *)((char *)ctx->ws_ojobs.p + obytes),
+                          (int)cjobs.size(), max_cn, ctx->stream),
+           "compose launch");
+        ctx->stats.launches++;
+    }
+    CK(cudaMemsetAsync(ctx->work_dev, 0, 2 * sizeof(unsigned long long), ctx->stream),
+       "cudaMemsetAsync");
     CK(cudaEventRecord(ctx->ev_a, ctx->stream), "cudaEventRecord");
     for (const Plan &p : plans) {
         KsgLaunch L{};
@@ -477,20 +518,25 @@ te_status run_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_ou
         L.dbg_nz = dbg_nz;
         L.dbg_out = dbg_out;
         L.jt = p.jt;
+        L.work = ctx->work_dev;
         CK(launch_ksg(L, p.v, p.items, p.dx1, p.smem, ctx->stream), "KSG kernel launch");
         ctx->stats.launches++;
         ctx->stats.ksg_launches++;
     }
     CK(cudaEventRecord(ctx->ev_b, ctx->stream), "cudaEventRecord");
+    CK(copy_d2h(ctx, ctx->work_host, ctx->work_dev, 2 * sizeof(unsigned long long)),
+       "cudaMemcpyAsync");
     CK(launch_finalize((const unsigned long long *)ctx->ws_acc.p, (long long *)ctx->ws_keys.p,
                        n_out, ctx->stream),
        "finalize launch");
     ctx->stats.launches++;
-    CK(cudaEventSynchronize(ctx->ev_b), "cudaEventSynchronize");
+    CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, ctx->ev_a, ctx->ev_b), "cudaEventElapsedTime");
     ctx->stats.kernel_ms += ms;
-    ctx->stats.pair_evals += pair_evals;
+    ctx->stats.pair_evals_bruteforce += pair_evals;
+    ctx->stats.pair_evals += ctx->work_host[0];
+    ctx->stats.ksg_ops += ctx->work_host[1];
     ctx->stats.estimates += members_total;
     return TE_OK;
 }
@@ -529,8 +575,10 @@ te_status te_ctx_create(int device, te_ctx **out)
     ctx->device = device;
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreate(&ctx->ev_a) != cudaSuccess || cudaEventCreate(&ctx->ev_b) != cudaSuccess) {
-        delete ctx;
+        cudaEventCreate(&ctx->ev_a) != cudaSuccess || cudaEventCreate(&ctx->ev_b) != cudaSuccess ||
+        cudaMalloc(&ctx->work_dev, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&ctx->work_host, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+        te_ctx_destroy(ctx);
         return TE_ECUDA;
     }
     ctx->stream = ctx->own_stream;
@@ -553,11 +601,13 @@ void te_ctx_destroy(te_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     DevBuf *bufs[] = {&ctx->ws_groups, &ctx->ws_members, &ctx->ws_cols,  &ctx->ws_acc,
                       &ctx->ws_keys,   &ctx->ws_perm,    &ctx->ws_stat,  &ctx->ws_dbg,
-                      &ctx->ws_order,  &ctx->ws_ojobs};
+                      &ctx->ws_order,  &ctx->ws_ojobs,  &ctx->ws_cperm};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->q_dev) cudaFree(ctx->q_dev);
     if (ctx->pin) cudaFreeHost(ctx->pin);
+    if (ctx->work_dev) cudaFree(ctx->work_dev);
+    if (ctx->work_host) cudaFreeHost(ctx->work_host);
     if (ctx->ev_a) cudaEventDestroy(ctx->ev_a);
     if (ctx->ev_b) cudaEventDestroy(ctx->ev_b);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);

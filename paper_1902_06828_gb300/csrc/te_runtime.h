@@ -60,11 +60,13 @@ struct te_ctx {
     int q_dev_len = 0;
     // grow-only device workspaces
     teksg::DevBuf ws_groups, ws_members, ws_cols, ws_acc, ws_keys, ws_perm, ws_stat, ws_dbg;
-    teksg::DevBuf ws_order, ws_ojobs;
+    teksg::DevBuf ws_order, ws_ojobs, ws_cperm;
     // pinned host staging
     void *pin = nullptr;
     size_t pin_cap = 0;
     te_stats stats{};
+    unsigned long long *work_dev = nullptr;   // executed-work counter of the KSG kernel
+    unsigned long long *work_host = nullptr;  // pinned copy
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     int prepared = 0;
 };
