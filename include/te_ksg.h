@@ -241,6 +241,44 @@ typedef struct {
 
 te_status te_get_stats(const te_ctx *ctx, te_stats *out);
 
+/* ---- allocation-free estimate (an addition of this library; the paper has no
+ * counterpart) ---------------------------------------------------------------
+ *
+ * cmi_ksg_static computes exactly what cmi_ksg computes (same estimator, same
+ * surrogate permutations, same keys and values) without allocating any device
+ * memory, for callers that cannot call cudaMalloc: a host framework that has
+ * already reserved the device for its own pool allocator, a serving process
+ * that budgets all device memory up front, or a latency-critical loop that
+ * cannot afford the device synchronisation of cudaMalloc / cudaFree.
+ *
+ * Its scratch memory (surrogate permutations, digamma table, launch
+ * descriptors, accumulators, keys) is one file-scope device array of
+ * TE_STATIC_SCRATCH_BYTES that every GPU which loads this library holds until
+ * the process exits.  A call needs
+ *   8 (N + 2) + 4 S N + 48 (S + 1) + 4 (dx + dy + dz)  bytes (each part
+ *   rounded up to 256), N = T - max_lag, S = n_surr <= TE_STATIC_MAX_SURR,
+ * and returns TE_EINVAL when that exceeds TE_STATIC_SCRATCH_BYTES.
+ *
+ * series_dev: device float32 [n_proc][T] on the current device, owned by the
+ * caller.  x, y, z, params: as cmi_ksg.  cuda_stream: a cudaStream_t of the
+ * current device or NULL (legacy default stream); the call synchronises it.
+ * out_cmi: host double[1 + S]; out_key: NULL or host int64[2 (1 + S)].
+ * Errors: status codes only (no context carries a message): TE_EINVAL for any
+ * rule cmi_ksg checks plus the scratch limit, TE_ECUDA for a failed CUDA call.
+ *
+ * The first call on a device resolves the device address of the scratch array
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the array, which keeps the last
+ * call's contents; each call clears what must start at zero.  Calls whose work
+ * overlaps on the GPU race on the array, and calls from several host threads
+ * race on static host buffers: serialise them. */
+#define TE_STATIC_SCRATCH_BYTES (32u << 20)
+#define TE_STATIC_MAX_SURR 4095
+te_status cmi_ksg_static(const float *series_dev, int32_t n_proc, int32_t T, const te_var *x,
+                         int32_t dx, const te_var *y, int32_t dy, const te_var *z, int32_t dz,
+                         const te_ksg_params *params, void *cuda_stream, double *out_cmi,
+                         int64_t *out_key);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,8 @@ from . import _abi
 from ._abi import TE_MAX_DIMS, TE_MAX_K  # noqa: F401
 
 __all__ = ["Context", "Data", "TEError", "te_data_create", "cmi_ksg", "cmi_ksg_debug",
-           "cmi_ksg_batch", "te_network_infer", "te_get_stats", "Job", "library_path"]
+           "cmi_ksg_batch", "te_network_infer", "te_get_stats", "Job", "library_path",
+           "cmi_ksg_static"]
 
 
 class TEError(RuntimeError):
@@ -299,3 +300,33 @@ def te_network_infer(ctx: Context, data: Data, *, k=4, theiler=0, max_lag_target
 
 def te_get_stats(ctx: Context) -> dict:
     return ctx.stats()
+
+
+def cmi_ksg_static(series_dev, x, y, z=(), *, k=4, theiler=0, max_lag=None, n_surr=0, seed=0,
+                   stream_tag=0, stream=None, return_keys=False):
+    """cmi_ksg without any device allocation, for callers that cannot
+    allocate device memory (see include/te_ksg.h).  series_dev: a CUDA float32
+    tensor [n_proc][T] on the current device; stream: None, an int handle or a
+    torch.cuda.Stream.  No context is involved; errors carry the status only."""
+    lib = _abi.load()
+    t = series_dev
+    if not (hasattr(t, "is_cuda") and t.is_cuda) or str(t.dtype) != "torch.float32":
+        raise TEError(_abi.TE_EINVAL, "series_dev must be a CUDA float32 tensor")
+    t = t.contiguous()
+    n_proc, T = t.shape
+    if max_lag is None:
+        max_lag = _default_max_lag(x, y, z)
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    xv, dx = _vars(x)
+    yv, dy = _vars(y)
+    zv, dz = _vars(z)
+    out = np.zeros(1 + max(int(n_surr), 0), np.float64)
+    keys = np.zeros(2 * out.size, np.int64)
+    p = _params(k, theiler, max_lag, n_surr, seed, stream_tag)
+    st = lib.cmi_ksg_static(C.c_void_p(t.data_ptr()), int(n_proc), int(T), xv, dx, yv, dy,
+                            zv if dz else None, dz, C.byref(p), C.c_void_p(stream or 0),
+                            out.ctypes.data, keys.ctypes.data)
+    if st != _abi.TE_OK:
+        raise TEError(st, "cmi_ksg_static failed")
+    return (out, _keys_to_int(keys)) if return_keys else out

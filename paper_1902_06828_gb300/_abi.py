@@ -85,6 +85,8 @@ SIGNATURES = {
                                    C.POINTER(C.POINTER(NetworkResult))]),
     "te_network_result_free": (None, [C.POINTER(NetworkResult)]),
     "te_get_stats": (C.c_int, [_P, C.POINTER(Stats)]),
+    "cmi_ksg_static": (C.c_int, [_P, _I32, _I32, C.POINTER(TeVar), _I32, C.POINTER(TeVar), _I32,
+                                 C.POINTER(TeVar), _I32, C.POINTER(KsgParams), _P, _P, _P]),
 }
 
 _lib = None

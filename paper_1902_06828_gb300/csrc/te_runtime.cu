@@ -145,6 +145,23 @@ int64_t dd_to_q(double h, double l)
 
 }  // namespace
 
+void digamma_q_fill(int n_max, int64_t *q)
+{
+    q[0] = 0;
+    if (n_max < 1) return;
+    double h, l;
+    euler_gamma_dd(h, l);
+    h = -h;
+    l = -l;
+    q[1] = dd_to_q(h, l);
+    for (int n = 2; n <= n_max; ++n) {
+        double rh, rl;
+        dd_recip((double)(n - 1), rh, rl);
+        dd_add(h, l, rh, rl, h, l);
+        q[n] = dd_to_q(h, l);
+    }
+}
+
 te_status ensure_q(te_ctx *ctx, int n_needed)
 {
     if ((int)ctx->q_host.size() <= n_needed) {

@@ -86,6 +86,8 @@ te_status cuda_fail(te_ctx *ctx, cudaError_t e, const char *what);
 te_status ensure_dev(te_ctx *ctx, DevBuf &b, size_t bytes);
 te_status ensure_pin(te_ctx *ctx, size_t bytes);
 te_status ensure_q(te_ctx *ctx, int n_needed);   // Q[0..n_needed] on the device
+// Q[0..n_max] into a caller buffer (host), same arithmetic as ensure_q
+void digamma_q_fill(int n_max, int64_t *q);
 
 // cudaMemcpyAsync on the context's stream, counted in ctx->stats
 cudaError_t copy_h2d(te_ctx *ctx, void *dst, const void *src, size_t bytes);
