@@ -154,6 +154,37 @@ def cpu_oracle_sample(series, params, budget_s=20.0, members=None):
                        f"oracle, {threads} OpenMP threads, {dt:.1f} s")}
 
 
+def plain_path(te, ctx, data, params, calls, stream):
+    """The plain path: one cmi_ksg call per estimate (no surrogates batched),
+    on a step-2-shaped estimate of target 0 (X = a source candidate, Y = the
+    target present, Z = its lag-1 past), timed call by call (host wall clock
+    around each blocking call), plus the latency of one request of the
+    batched form (the same estimate with its 200 surrogates in one call)."""
+    import torch
+    n_proc = data.n_proc
+    ml = max(params["max_lag_target"], params["max_lag_sources"])
+    cands = [(q, l) for q in range(1, n_proc) for l in range(1, params["max_lag_sources"] + 1)]
+
+    def one(c, S):
+        t = time.perf_counter()
+        te.cmi_ksg(ctx, data, [c], [(0, 0)], [(0, 1)], k=params["k"], max_lag=ml, n_surr=S,
+                   seed=params["seed"], stream_tag=7)
+        return time.perf_counter() - t
+
+    one(cands[0], 0)
+    one(cands[0], 200)
+    lat = [one(cands[a % len(cands)], 0) for a in range(calls)]
+    req = [one(cands[a % len(cands)], 200) for a in range(max(3, calls // 3))]
+    lat_ms = np.array(lat) * 1e3
+    req_ms = np.array(req) * 1e3
+    return {"value": calls / float(np.sum(lat)), "unit": UNIT, "calls": calls,
+            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+            "request_201_p50_ms": float(np.percentile(req_ms, 50)),
+            "request_201_p99_ms": float(np.percentile(req_ms, 99)),
+            "request_201_estimates_per_s": 201 * len(req) / float(np.sum(req)),
+            "shape": "X=(q,l) candidate, Y=(0,0), Z=(0,1), N=%d, k=%d" % (data.T - ml, params["k"])}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -163,7 +194,7 @@ def run_reference(args):
     threads = oksg.max_threads()
     # size one step to ~20 s of CPU work
     calib = cpu_oracle_sample(series, params, members=threads)
-    per_member = calib["cores"] / calib["value"]
+    per_member = 1.0 / calib["value"]          # seconds per member with all threads busy
     members = max(threads, int(20.0 / per_member) // threads * threads)
     for _ in range(args.warmup):
         cpu_oracle_sample(series, params, members=threads)
@@ -200,6 +231,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--targets", default="all", help="comma list of targets, or 'all'")
+    ap.add_argument("--plain-calls", type=int, default=30,
+                    help="one-call-per-estimate calls timed for the plain-path comparison")
     args = ap.parse_args()
 
     if args.impl == "reference":
@@ -324,6 +357,9 @@ def main():
                      else None},
         "clocks": clk,
     }
+    if args.plain_calls > 0:
+        line["plain_path"] = plain_path(te, ctx, data, params, args.plain_calls, stream)
+        line["plain_path"]["batched_over_plain"] = value / line["plain_path"]["value"]
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_oracle_sample(series, params)
     print(json.dumps(line), flush=True)
