@@ -311,14 +311,8 @@ def main():
     se = ctx.stats()
     e_ms = e0.elapsed_time(e1)
 
-    t = torch.tensor([ms, e_ms, float(n_est), float(e_est)], dtype=torch.float64, device="cuda")
-    if dist:
-        mx = t[:2].clone()
-        sm = t[2:].clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms, e_ms = mx.tolist()
-        n_est, e_est = sm.tolist()
+    from paper_1902_06828_gb300.shard import combine_timing
+    (ms, e_ms), (n_est, e_est) = combine_timing(dist, [ms, e_ms], [n_est, e_est], device="cuda")
     if rank != 0:
         if dist:
             dist.destroy_process_group()
