@@ -241,6 +241,62 @@ typedef struct {
 
 te_status te_get_stats(const te_ctx *ctx, te_stats *out);
 
+/* ---- serving: continuous batching ------------------------------------------
+ *
+ * Jobs (te_cmi_job, as for cmi_ksg_batch) are submitted from any host thread
+ * and evaluated by a scheduler thread of the context.  Pending jobs are
+ * admitted in arrival order while the device memory of the admitted jobs stays
+ * within hbm_budget_bytes; each admitted set is fused into one batch, and up to
+ * max_inflight batches run on the device at once, each on its own stream.
+ * Jobs submitted while batches run join the next batch.  A job's result does
+ * not depend on the batch it lands in (exact keys), so it equals cmi_ksg's.
+ * Data sets stay resident on the device (te_data) across jobs.
+ * (Supporting Information, Run-time on CPU and GPU: targets are independent
+ * and may be analysed concurrently.)
+ */
+typedef uint64_t te_ticket;
+
+typedef struct {
+    size_t hbm_budget_bytes;  /* device bytes admitted jobs may hold at once (0: 4 GiB); a job
+                                 needs about 8 S N + 4 N (1 + dy + dz) + 64 (S + 1) bytes */
+    int32_t max_inflight;     /* batches on the device at once, 1..8 (0: 2) */
+    int32_t max_batch_jobs;   /* jobs per batch (0: 2048) */
+} te_serve_config;
+
+typedef struct {
+    uint64_t submitted, completed, cancelled, batches;
+    size_t in_use_bytes, peak_bytes;   /* admitted footprint now / at most */
+    uint64_t pending;                  /* jobs waiting for admission */
+} te_serve_stats;
+
+/* Start serving on ctx with cfg (NULL: defaults).  te_serve_submit starts it
+ * with defaults when needed.  Errors: TE_EINVAL (already started, bad cfg),
+ * TE_ECUDA / TE_ENOMEM (streams or host state could not be created). */
+te_status te_serve_start(te_ctx *ctx, const te_serve_config *cfg);
+
+/* Queue one job; *out receives its ticket.  The job's arrays are copied, the
+ * data set must stay alive until the job is polled.  Thread-safe.
+ * Errors: TE_EINVAL (as cmi_ksg), TE_EBUSY (the job alone exceeds the budget). */
+te_status te_serve_submit(te_ctx *ctx, const te_cmi_job *job, te_ticket *out);
+
+/* Wait up to timeout_ms (< 0: no limit) for the job, then copy its results:
+ * out host double[1 + S], out_key NULL or host int64[2 (1 + S)], as cmi_ksg.
+ * A ticket is released by the poll that returns TE_OK, TE_ECANCELLED or an
+ * error; TE_ETIMEOUT keeps it.  Thread-safe.  Errors: TE_EINVAL (unknown
+ * ticket), TE_ETIMEOUT, TE_ECANCELLED, or the job's CUDA error. */
+te_status te_serve_poll(te_ctx *ctx, te_ticket ticket, int32_t timeout_ms, double *out,
+                        int64_t *out_key);
+
+/* Cancel a job: a pending job never runs; a running job's results are
+ * discarded.  Its next poll returns TE_ECANCELLED.  Thread-safe. */
+te_status te_serve_cancel(te_ctx *ctx, te_ticket ticket);
+
+/* Stop serving: pending jobs are cancelled, running batches finish, the
+ * scheduler thread exits.  te_ctx_destroy calls it. */
+te_status te_serve_stop(te_ctx *ctx);
+
+te_status te_serve_get_stats(te_ctx *ctx, te_serve_stats *out);
+
 /* ---- allocation-free estimate (an addition of this library; the paper has no
  * counterpart) ---------------------------------------------------------------
  *

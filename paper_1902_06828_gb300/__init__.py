@@ -26,7 +26,8 @@ from ._abi import TE_MAX_DIMS, TE_MAX_K  # noqa: F401
 
 __all__ = ["Context", "Data", "TEError", "te_data_create", "cmi_ksg", "cmi_ksg_debug",
            "cmi_ksg_batch", "te_network_infer", "te_get_stats", "Job", "library_path",
-           "cmi_ksg_static"]
+           "cmi_ksg_static", "te_serve_start", "te_serve_submit", "te_serve_poll",
+           "te_serve_cancel", "te_serve_stop", "te_serve_get_stats"]
 
 
 class TEError(RuntimeError):
@@ -300,6 +301,65 @@ def te_network_infer(ctx: Context, data: Data, *, k=4, theiler=0, max_lag_target
 
 def te_get_stats(ctx: Context) -> dict:
     return ctx.stats()
+
+
+def _job_struct(j, keep):
+    ml = j.max_lag if j.max_lag is not None else _default_max_lag(j.x, j.y, j.z)
+    xv, dx = _vars(j.x)
+    yv, dy = _vars(j.y)
+    zv, dz = _vars(j.z)
+    keep += [xv, yv, zv]
+    js = _abi.CmiJob()
+    js.data = j.data._h
+    js.x = C.cast(xv, C.POINTER(_abi.TeVar))
+    js.y = C.cast(yv, C.POINTER(_abi.TeVar))
+    js.z = C.cast(zv, C.POINTER(_abi.TeVar)) if dz else None
+    js.dx, js.dy, js.dz = dx, dy, dz
+    js.params = _params(j.k, j.theiler, ml, j.n_surr, j.seed, j.stream_tag)
+    return js
+
+
+def te_serve_start(ctx: Context, hbm_budget_bytes=0, max_inflight=0, max_batch_jobs=0):
+    cfg = _abi.ServeConfig(int(hbm_budget_bytes), int(max_inflight), int(max_batch_jobs))
+    _check(ctx._h, ctx._lib.te_serve_start(ctx._h, C.byref(cfg)))
+
+
+def te_serve_submit(ctx: Context, job: "Job") -> int:
+    """Queue a job (thread-safe) -> ticket."""
+    keep = []
+    js = _job_struct(job, keep)
+    t = C.c_uint64()
+    st = ctx._lib.te_serve_submit(ctx._h, C.byref(js), C.byref(t))
+    if st != _abi.TE_OK:
+        raise TEError(st, "te_serve_submit rejected the job")
+    return int(t.value)
+
+
+def te_serve_poll(ctx: Context, ticket: int, n_surr: int, timeout_ms: int = -1,
+                  return_keys=False):
+    """Wait for a job's results (float64 [1 + n_surr]); raises TEError with
+    TE_ETIMEOUT (ticket kept) or TE_ECANCELLED."""
+    out = np.zeros(1 + int(n_surr), np.float64)
+    keys = np.zeros(2 * out.size, np.int64)
+    st = ctx._lib.te_serve_poll(ctx._h, int(ticket), int(timeout_ms), out.ctypes.data,
+                                keys.ctypes.data)
+    if st != _abi.TE_OK:
+        raise TEError(st, "te_serve_poll")
+    return (out, _keys_to_int(keys)) if return_keys else out
+
+
+def te_serve_cancel(ctx: Context, ticket: int):
+    _check(ctx._h, ctx._lib.te_serve_cancel(ctx._h, int(ticket)))
+
+
+def te_serve_stop(ctx: Context):
+    _check(ctx._h, ctx._lib.te_serve_stop(ctx._h))
+
+
+def te_serve_get_stats(ctx: Context) -> dict:
+    s = _abi.ServeStats()
+    _check(ctx._h, ctx._lib.te_serve_get_stats(ctx._h, C.byref(s)))
+    return {f: getattr(s, f) for f, _ in s._fields_}
 
 
 def cmi_ksg_static(series_dev, x, y, z=(), *, k=4, theiler=0, max_lag=None, n_surr=0, seed=0,

@@ -65,6 +65,17 @@ class Stats(C.Structure):
                 ("pair_evals_bruteforce", C.c_uint64), ("ksg_ops", C.c_uint64)]
 
 
+class ServeConfig(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_inflight", C.c_int32),
+                ("max_batch_jobs", C.c_int32)]
+
+
+class ServeStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("cancelled", C.c_uint64),
+                ("batches", C.c_uint64), ("in_use_bytes", C.c_size_t), ("peak_bytes", C.c_size_t),
+                ("pending", C.c_uint64)]
+
+
 # every symbol include/te_ksg.h declares: name -> (restype, argtypes)
 _P = C.c_void_p
 _I32 = C.c_int32
@@ -85,6 +96,12 @@ SIGNATURES = {
                                    C.POINTER(C.POINTER(NetworkResult))]),
     "te_network_result_free": (None, [C.POINTER(NetworkResult)]),
     "te_get_stats": (C.c_int, [_P, C.POINTER(Stats)]),
+    "te_serve_start": (C.c_int, [_P, C.POINTER(ServeConfig)]),
+    "te_serve_submit": (C.c_int, [_P, C.POINTER(CmiJob), C.POINTER(C.c_uint64)]),
+    "te_serve_poll": (C.c_int, [_P, C.c_uint64, _I32, _P, _P]),
+    "te_serve_cancel": (C.c_int, [_P, C.c_uint64]),
+    "te_serve_stop": (C.c_int, [_P]),
+    "te_serve_get_stats": (C.c_int, [_P, C.POINTER(ServeStats)]),
     "cmi_ksg_static": (C.c_int, [_P, _I32, _I32, C.POINTER(TeVar), _I32, C.POINTER(TeVar), _I32,
                                  C.POINTER(TeVar), _I32, C.POINTER(KsgParams), _P, _P, _P]),
 }

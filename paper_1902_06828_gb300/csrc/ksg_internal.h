@@ -116,6 +116,18 @@ inline size_t ksg_smem_bytes(int rows_t, int rows_q, int jt, int qt)
 cudaError_t launch_perms(int32_t *out, long long stride, int n, uint64_t seed, uint64_t target,
                          uint64_t stage, uint64_t iter, int s_first, int n_perm, cudaStream_t st);
 
+// Many requests of launch_perms in one launch; request r writes n_perm
+// permutations of [0, n) at out (stride n) for s = s_first .. s_first+n_perm-1,
+// and owns launch CTAs perm_begin .. perm_begin + n_perm - 1.
+struct PermJob {
+    int32_t *out;
+    int n, n_perm, s_first;
+    uint64_t seed, target, stage, iter;
+    long long perm_begin;
+};
+cudaError_t launch_perms_multi(const PermJob *jobs, int n_jobs, long long total, int max_n,
+                               cudaStream_t st);
+
 // acc (low, high partial sums) -> normalised 128-bit keys (hi, lo) per slot.
 cudaError_t launch_finalize(const unsigned long long *acc, long long *keys, int n_out,
                             cudaStream_t st);

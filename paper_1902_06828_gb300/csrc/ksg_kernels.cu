@@ -1088,6 +1088,44 @@ __global__ void compose_kernel(const ComposeJob *jobs)
         J.out[p] = J.perm[J.sigma[p]];
 }
 
+// Many permutation requests in one launch: CTA g is permutation g of the
+// concatenated request list (binary search over the requests' first index).
+__global__ void fisher_yates_multi_kernel(const PermJob *jobs, int n_jobs, int smem_n)
+{
+    extern __shared__ int32_t sperm[];
+    const long long g = blockIdx.x;
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].perm_begin <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    const PermJob J = jobs[lo];
+    const int r = (int)(g - J.perm_begin);
+    const int n = J.n;
+    const bool in_smem = n <= smem_n;
+    int32_t *dst = J.out + (long long)r * n;
+    int32_t *p = in_smem ? sperm : dst;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = i;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t h = sm64_once(J.seed ^ J.target);
+        h = sm64_once(h ^ J.stage);
+        h = sm64_once(h ^ J.iter);
+        uint64_t st = sm64_once(h ^ (uint64_t)(J.s_first + r));
+        for (int i = n - 1; i >= 1; --i) {
+            const uint64_t rr = sm64_next(st);
+            const int j = (int)__umul64hi(rr, (uint64_t)(i + 1));
+            const int32_t t = p[i];
+            p[i] = p[j];
+            p[j] = t;
+        }
+    }
+    __syncthreads();
+    if (in_smem)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = sperm[i];
+}
+
 __global__ void finalize_kernel(const unsigned long long *acc, long long *keys, int n_out)
 {
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1245,6 +1283,25 @@ cudaError_t launch_perms(int32_t *out, long long stride, int n, uint64_t seed, u
     }
     fisher_yates_kernel<<<n_perm, 256, in_smem ? smem : 0, st>>>(out, stride, n, seed, target,
                                                                 stage, iter, s_first, in_smem);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_perms_multi(const PermJob *jobs, int n_jobs, long long total, int max_n,
+                               cudaStream_t st)
+{
+    if (n_jobs <= 0 || total <= 0) return cudaSuccess;
+    if (total > 0x7fffffffLL) return cudaErrorInvalidValue;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(
+            reinterpret_cast<const void *>(&fisher_yates_multi_kernel),
+            cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    const int smem_n = max_n * 4 <= 200 * 1024 ? max_n : 0;
+    fisher_yates_multi_kernel<<<(unsigned)total, 256, (size_t)smem_n * 4, st>>>(jobs, n_jobs,
+                                                                               smem_n);
     return cudaGetLastError();
 }
 

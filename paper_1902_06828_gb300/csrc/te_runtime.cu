@@ -206,37 +206,48 @@ double key_to_cmi(const te_ctx *ctx, int64_t hi, uint64_t lo, int k, int N)
     return psi_k + t / d;
 }
 
-te_status validate_estimate(te_ctx *ctx, const te_data *data, const te_var *x, int dx,
-                            const te_var *y, int dy, const te_var *z, int dz, int k, int theiler,
-                            int max_lag, int n_surr)
+te_status check_estimate(const te_ctx *ctx, const te_data *data, const te_var *x, int dx,
+                         const te_var *y, int dy, const te_var *z, int dz, int k, int theiler,
+                         int max_lag, int n_surr, std::string &msg)
 {
-    if (!data) return fail(ctx, TE_EINVAL, "data is NULL");
-    if (data->ctx != ctx) return fail(ctx, TE_EINVAL, "data belongs to another context");
-    if (!x || dx < 1) return fail(ctx, TE_EINVAL, "x needs at least one variable");
-    if (!y || dy < 1) return fail(ctx, TE_EINVAL, "y needs at least one variable");
-    if (dz < 0 || (dz > 0 && !z)) return fail(ctx, TE_EINVAL, "z is NULL with dz > 0");
+    if (!data) return (msg = "data is NULL", TE_EINVAL);
+    if (data->ctx != ctx) return (msg = "data belongs to another context", TE_EINVAL);
+    if (!x || dx < 1) return (msg = "x needs at least one variable", TE_EINVAL);
+    if (!y || dy < 1) return (msg = "y needs at least one variable", TE_EINVAL);
+    if (dz < 0 || (dz > 0 && !z)) return (msg = "z is NULL with dz > 0", TE_EINVAL);
     if (dx + dy + dz > TE_MAX_DIMS)
-        return fail(ctx, TE_EINVAL, "dx + dy + dz exceeds TE_MAX_DIMS (32)");
-    if (k < 1 || k > TE_MAX_K) return fail(ctx, TE_EINVAL, "k must be in 1..16");
-    if (theiler < 0) return fail(ctx, TE_EINVAL, "theiler window must be >= 0");
-    if (n_surr < 0) return fail(ctx, TE_EINVAL, "n_surr must be >= 0");
+        return (msg = "dx + dy + dz exceeds TE_MAX_DIMS (32)", TE_EINVAL);
+    if (k < 1 || k > TE_MAX_K) return (msg = "k must be in 1..16", TE_EINVAL);
+    if (theiler < 0) return (msg = "theiler window must be >= 0", TE_EINVAL);
+    if (n_surr < 0) return (msg = "n_surr must be >= 0", TE_EINVAL);
     if (max_lag < 0 || max_lag >= data->T)
-        return fail(ctx, TE_EINVAL, "max_lag must be in 0..T-1");
+        return (msg = "max_lag must be in 0..T-1", TE_EINVAL);
     const long long N = (long long)data->T - max_lag;
     if (N - 1 - 2LL * theiler < k)
-        return fail(ctx, TE_EINVAL, "fewer than k valid neighbours for some point "
-                                    "(N - 1 - 2 theiler < k)");
+        return (msg = "fewer than k valid neighbours for some point "
+                                    "(N - 1 - 2 theiler < k)", TE_EINVAL);
     const te_var *vs[3] = {x, y, z};
     const int ds[3] = {dx, dy, dz};
     for (int s = 0; s < 3; ++s)
         for (int d = 0; d < ds[s]; ++d) {
             const te_var v = vs[s][d];
             if (v.proc < 0 || v.proc >= data->n_proc)
-                return fail(ctx, TE_EINVAL, "variable process outside the data");
+                return (msg = "variable process outside the data", TE_EINVAL);
             if (v.lag < 0 || v.lag > max_lag)
-                return fail(ctx, TE_EINVAL, "variable lag outside 0..max_lag");
+                return (msg = "variable lag outside 0..max_lag", TE_EINVAL);
         }
     return TE_OK;
+}
+
+te_status validate_estimate(te_ctx *ctx, const te_data *data, const te_var *x, int dx,
+                            const te_var *y, int dy, const te_var *z, int dz, int k, int theiler,
+                            int max_lag, int n_surr)
+{
+    std::string msg;
+    const te_status st =
+        check_estimate(ctx, data, x, dx, y, dy, z, dz, k, theiler, max_lag, n_surr, msg);
+    if (st) ctx->err = msg;
+    return st;
 }
 
 // ---- engine ----------------------------------------------------------------
@@ -256,6 +267,30 @@ struct ClassKey {
 te_status run_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_out, int dbg_out,
                      float *dbg_eps, int *dbg_nxz, int *dbg_nyz, int *dbg_nz)
 {
+    te_status st = launch_groups(ctx, groups, n_out, dbg_out, dbg_eps, dbg_nxz, dbg_nyz, dbg_nz);
+    if (st) return st;
+    return finish_groups(ctx);
+}
+
+te_status finish_groups(te_ctx *ctx)
+{
+    CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    if (!ctx->pend_timed) return TE_OK;
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev_a, ctx->ev_b), "cudaEventElapsedTime");
+    ctx->stats.kernel_ms += ms;
+    ctx->stats.pair_evals_bruteforce += ctx->pend_pair_evals;
+    ctx->stats.pair_evals += ctx->work_host[0];
+    ctx->stats.ksg_ops += ctx->work_host[1];
+    ctx->stats.estimates += ctx->pend_members;
+    ctx->pend_timed = 0;
+    return TE_OK;
+}
+
+te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_out, int dbg_out,
+                        float *dbg_eps, int *dbg_nxz, int *dbg_nyz, int *dbg_nz)
+{
+    ctx->pend_timed = 0;
     te_status st;
     int max_N = 0;
     for (const HostGroup &g : groups) max_N = std::max(max_N, g.data->T - g.max_lag);
@@ -547,14 +582,9 @@ te_status run_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_ou
                        n_out, ctx->stream),
        "finalize launch");
     ctx->stats.launches++;
-    CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, ctx->ev_a, ctx->ev_b), "cudaEventElapsedTime");
-    ctx->stats.kernel_ms += ms;
-    ctx->stats.pair_evals_bruteforce += pair_evals;
-    ctx->stats.pair_evals += ctx->work_host[0];
-    ctx->stats.ksg_ops += ctx->work_host[1];
-    ctx->stats.estimates += members_total;
+    ctx->pend_timed = 1;
+    ctx->pend_pair_evals = pair_evals;
+    ctx->pend_members = members_total;
     return TE_OK;
 }
 
@@ -614,6 +644,7 @@ te_status te_ctx_set_stream(te_ctx *ctx, void *cuda_stream)
 void te_ctx_destroy(te_ctx *ctx)
 {
     if (!ctx) return;
+    te_serve_stop(ctx);
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     DevBuf *bufs[] = {&ctx->ws_groups, &ctx->ws_members, &ctx->ws_cols,  &ctx->ws_acc,

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -65,6 +66,11 @@ struct te_ctx {
     void *pin = nullptr;
     size_t pin_cap = 0;
     te_stats stats{};
+    // counters of the launch in flight, added to stats by finish_groups
+    int pend_timed = 0;
+    uint64_t pend_pair_evals = 0, pend_members = 0;
+    struct te_server *server = nullptr;   // serving state (te_serve_*), created on demand
+    std::mutex serve_start_mu;
     unsigned long long *work_dev = nullptr;   // executed-work counter of the KSG kernel
     unsigned long long *work_host = nullptr;  // pinned copy
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
@@ -93,7 +99,11 @@ void digamma_q_fill(int n_max, int64_t *q);
 cudaError_t copy_h2d(te_ctx *ctx, void *dst, const void *src, size_t bytes);
 cudaError_t copy_d2h(te_ctx *ctx, void *dst, const void *src, size_t bytes);
 
-// Validate one estimate's variables against its data and parameters.
+// Validate one estimate's variables against its data and parameters: the pure
+// form reports through msg (safe from any thread); the other sets ctx->err.
+te_status check_estimate(const te_ctx *ctx, const te_data *data, const te_var *x, int dx,
+                         const te_var *y, int dy, const te_var *z, int dz, int k, int theiler,
+                         int max_lag, int n_surr, std::string &msg);
 te_status validate_estimate(te_ctx *ctx, const te_data *data, const te_var *x, int dx,
                             const te_var *y, int dy, const te_var *z, int dz, int k, int theiler,
                             int max_lag, int n_surr);
@@ -103,6 +113,13 @@ te_status validate_estimate(te_ctx *ctx, const te_data *data, const te_var *x, i
 te_status run_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_out,
                      int dbg_out = -1, float *dbg_eps = nullptr, int *dbg_nxz = nullptr,
                      int *dbg_nyz = nullptr, int *dbg_nz = nullptr);
+
+// The same work in two halves: launch_groups queues everything on ctx->stream
+// (keys land in ctx->ws_keys); finish_groups synchronises and updates stats.
+te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_out,
+                        int dbg_out = -1, float *dbg_eps = nullptr, int *dbg_nxz = nullptr,
+                        int *dbg_nyz = nullptr, int *dbg_nz = nullptr);
+te_status finish_groups(te_ctx *ctx);
 
 double key_to_cmi(const te_ctx *ctx, int64_t hi, uint64_t lo, int k, int N);
 

@@ -1,0 +1,99 @@
+"""Serving (continuous batching): results in the mix equal results alone.
+
+Jobs of uneven shape (three data sets of different T, joint dims 2-8,
+different surrogate counts and k) are submitted from several host threads
+while batches run; each job's keys must equal the same job run alone through
+cmi_ksg, bit for bit, and its values within the parity tolerance."""
+import threading
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+REL, ABS = 1e-9, 1e-12
+
+
+@pytest.fixture(scope="module")
+def env():
+    import paper_1902_06828_gb300 as te
+    ctx = te.Context(0)
+    yield te, ctx
+    ctx.close()
+
+
+def _jobs(te, ctx, rng):
+    sets = []
+    for T, seed in ((600, 1), (1100, 2), (1700, 3)):
+        x, _, _ = synth.var_er(n=6, p=0.4, T=T, seed=seed, max_lag=3)
+        sets.append(te.te_data_create(ctx, synth.standardise_jitter(x, seed)))
+    jobs = []
+    for a in range(36):
+        d = sets[a % 3]
+        tgt = int(rng.integers(0, 6))
+        src = [(int(q), int(l)) for q, l in zip(rng.integers(0, 6, 2), rng.integers(1, 4, 2))]
+        x = src[:1] if a % 5 else src
+        z = [(tgt, l) for l in range(1, int(rng.integers(1, 4)) + 1)]
+        if a % 7 == 0:
+            z = []
+        jobs.append(te.Job(d, x, [(tgt, 0)], z, k=4 if a % 4 else 3, max_lag=3,
+                           n_surr=int(rng.choice([0, 9, 40, 120])), seed=5, stream_tag=a))
+    return jobs
+
+
+def test_mixed_jobs_equal_alone(env):
+    te, ctx = env
+    rng = np.random.default_rng(0)
+    jobs = _jobs(te, ctx, rng)
+    alone = [te.cmi_ksg(ctx, j.data, j.x, j.y, j.z, k=j.k, max_lag=j.max_lag, n_surr=j.n_surr,
+                        seed=j.seed, stream_tag=j.stream_tag, return_keys=True) for j in jobs]
+    te.te_serve_start(ctx, max_inflight=2, max_batch_jobs=5)
+    results = [None] * len(jobs)
+
+    def worker(idx):
+        for a in idx:
+            t = te.te_serve_submit(ctx, jobs[a])
+            results[a] = te.te_serve_poll(ctx, t, jobs[a].n_surr, return_keys=True)
+
+    threads = [threading.Thread(target=worker, args=(list(range(w, len(jobs), 4)),))
+               for w in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    st = te.te_serve_get_stats(ctx)
+    assert st["completed"] == len(jobs) and st["batches"] >= 2
+    for (ref, rkeys), (got, gkeys) in zip(alone, results):
+        assert gkeys == rkeys
+        assert np.all(np.abs(got - ref) <= REL * np.abs(ref) + ABS)
+    # submit everything at once, then poll in reverse order
+    tickets = [te.te_serve_submit(ctx, j) for j in jobs]
+    for a in reversed(range(len(jobs))):
+        got, gkeys = te.te_serve_poll(ctx, tickets[a], jobs[a].n_surr, return_keys=True)
+        assert gkeys == alone[a][1]
+    te.te_serve_stop(ctx)
+
+
+def test_cancel_budget_and_timeout(env):
+    te, ctx = env
+    w = synth.workload_var10(T=10000, seed=3)
+    d = te.te_data_create(ctx, w["series"])
+    te.te_serve_start(ctx, hbm_budget_bytes=256 << 20, max_inflight=1, max_batch_jobs=1)
+    big = te.Job(d, [(1, 1)], [(0, 0)], [(0, 1)], k=4, max_lag=5, n_surr=400, seed=1)
+    huge = te.Job(d, [(1, 1)], [(0, 0)], [(0, 1)], k=4, max_lag=5, n_surr=4000, seed=1)
+    with pytest.raises(te.TEError, match="TE_EBUSY"):
+        te.te_serve_submit(ctx, huge)          # 8 S N bytes > 256 MiB
+    t1 = te.te_serve_submit(ctx, big)
+    t2 = te.te_serve_submit(ctx, big)          # waits behind t1 (one job per batch)
+    te.te_serve_cancel(ctx, t2)
+    with pytest.raises(te.TEError, match="TE_ECANCELLED"):
+        te.te_serve_poll(ctx, t2, 400)
+    with pytest.raises(te.TEError, match="TE_ETIMEOUT"):
+        te.te_serve_poll(ctx, t1, 400, timeout_ms=0)
+    got = te.te_serve_poll(ctx, t1, 400)
+    ref = te.cmi_ksg(ctx, d, [(1, 1)], [(0, 0)], [(0, 1)], k=4, max_lag=5, n_surr=400, seed=1)
+    assert np.array_equal(got, ref)
+    with pytest.raises(te.TEError, match="TE_EINVAL"):
+        te.te_serve_poll(ctx, t1, 400)         # released
+    te.te_serve_stop(ctx)
