@@ -31,6 +31,8 @@ struct GroupDesc {
     const float *yz;
     const float2 *box;
     int n_chunks8;
+    const float2 *tbox;     // [dy + dz][n_tiles256]: (min, max) per aligned 256-point tile
+    int n_tiles256;
 };
 
 // One spatial-order job (one CTA): Morton keys of the (Y, Z) coordinates of a
@@ -42,6 +44,7 @@ struct OrderJob {
     int *sigma;
     float *yz;
     float2 *box;
+    float2 *tbox;           // boxes of aligned 256-point tiles
 };
 constexpr int kMaxOrderN = 16384;   // points a CTA can sort in shared memory
 cudaError_t launch_order(const OrderJob *jobs, int n_jobs, cudaStream_t st);

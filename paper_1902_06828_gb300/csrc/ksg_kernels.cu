@@ -592,6 +592,7 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
     __shared__ long long s_red[LW][32];
     __shared__ int s_clist[kMaxLaneChunks];   // live chunks of the current tile
     __shared__ int s_nlive;
+    __shared__ float2 s_cqbox[32];
 
     // ---- this lane's member ----
     const int mi = mb * 32 + lane;
@@ -627,6 +628,30 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
     }
     if (lane < LQ) s_bound[warp][lane] = CUDART_INF_F;
     __syncthreads();
+    // bounding box of the CTA's 32 query points, for the coarse tile test
+    if (sorted && warp == 0) {
+        for (int d = 0; d < dyz; ++d) {
+            const float v = s_q[lane * dyz + d];   // query lane of the CTA (warp lane/4, a lane%4)
+            const float mn = warp_min(v), mx = warp_max(v);
+            if (lane == 0) s_cqbox[d] = make_float2(mn, mx);
+        }
+    }
+    __syncthreads();
+    // coarse test, taken identically by every thread: only values that no
+    // thread writes before the next barrier are read (s_bound, s_cqbox, tbox)
+    const bool coarse = sorted && jt == 256 && G.tbox != nullptr;
+    auto tile_dead = [&](int t, bool pass1) {
+        if (!coarse) return false;
+        float bound = 0.f;
+        for (int e = 0; e < LW * LQ; ++e) bound = fmaxf(bound, (&s_bound[0][0])[e]);
+        float lb = 0.f;
+        for (int d = pass1 ? 0 : dy; d < dyz; ++d) {
+            const float2 b = G.tbox[(size_t)d * G.n_tiles256 + t];
+            const float2 q = s_cqbox[d];
+            lb = fmaxf(lb, fmaxf(fmaxf(__fsub_rn(b.x, q.y), __fsub_rn(q.x, b.y)), 0.f));
+        }
+        return lb >= bound;
+    };
     const bool shared_perm = s_shared_perm != 0;
     const int32_t *perm0 = s_mperm[0];
 
@@ -754,6 +779,10 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
 
     const int ntiles = (N + jt - 1) / jt;
     unsigned executed1 = 0, executed2 = 0;
+    // s_live is double-buffered by the count of liveness checks taken (not by
+    // tile): two checks that use the same buffer always have the barrier of the
+    // check between them in between, also when tiles are skipped without one
+    int nchk = 0;
 
     // ---------------- pass 1: k nearest joint distances ----------------
     float buf[LQ][KB];
@@ -776,16 +805,18 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
             toggle = !toggle;
             const int j0 = t * jt;
             const int jn = min(jt, N - j0);
+            if (tile_dead(t, true)) continue;
             if (sorted) {
                 load_boxes(j0, jn);
                 __syncthreads();
             }
             const bool live = tile_live(j0, jn, true);
-            if (lane == 0) s_live[s & 1][warp] = live;
+            const int buf_i = nchk++ & 1;
+            if (lane == 0) s_live[buf_i][warp] = live;
             __syncthreads();
             int any = 0;
 #pragma unroll
-            for (int b = 0; b < LW; ++b) any |= s_live[s & 1][b];
+            for (int b = 0; b < LW; ++b) any |= s_live[buf_i][b];
             if (!any) continue;
             build_list();
             stage(j0);
@@ -834,6 +865,11 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
         }
     }
 
+    // Warps leave pass 1 at different times (coarse skips take no barrier);
+    // none may overwrite s_bound with pass-2 values while another still reads
+    // it for a pass-1 coarse test.
+    __syncthreads();
+
     // ---------------- pass 2: strict range counts ----------------
     float eps[LQ], cz[LQ], cxz[LQ], cyz[LQ];
 #pragma unroll
@@ -847,11 +883,12 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
         const float em = warp_max(eps[a]);
         if (lane == 0) s_bound[warp][a] = prune2 ? em : CUDART_INF_F;
     }
-    __syncwarp();
+    __syncthreads();   // every warp's pass-2 bounds before the coarse tile test
     for (int t = 0; t < ntiles; ++t) {
         const int j0 = t * jt;
         const int jn = min(jt, N - j0);
         bool live = true;
+        if (prune2 && tile_dead(t, false)) continue;
         if (prune2) {
             load_boxes(j0, jn);
             __syncthreads();
@@ -867,11 +904,12 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
             }
             __syncwarp();
         }
-        if (lane == 0) s_live[t & 1][warp] = live;
+        const int buf_i = nchk++ & 1;
+        if (lane == 0) s_live[buf_i][warp] = live;
         __syncthreads();
         int any = 0;
 #pragma unroll
-        for (int b = 0; b < LW; ++b) any |= s_live[t & 1][b];
+        for (int b = 0; b < LW; ++b) any |= s_live[buf_i][b];
         if (!any) continue;
         build_list();
         stage(j0);
@@ -1076,6 +1114,17 @@ __global__ void __launch_bounds__(1024) order_kernel(const OrderJob *jobs)
             mx = fmaxf(mx, v);
         }
         J.box[(size_t)d * nch + c] = make_float2(mn, mx);
+    }
+    const int ntl = (N + 255) >> 8;
+    for (int e = tid; e < ntl * D; e += blockDim.x) {
+        const int d = e / ntl, c = e - d * ntl;
+        float mn = CUDART_INF_F, mx = -CUDART_INF_F;
+        for (int p = 256 * c; p < min(256 * c + 256, N); ++p) {
+            const float v = base[J.cols[d] + (int)(skeys[p] & 0x3FFFull)];
+            mn = fminf(mn, v);
+            mx = fmaxf(mx, v);
+        }
+        J.tbox[(size_t)d * ntl + c] = make_float2(mn, mx);
     }
 }
 

@@ -308,8 +308,8 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
     // Spatial order for every group without a Theiler window that fits one
     // sorting CTA: sigma [N], sorted coordinates [dyz][N], chunk boxes.
     struct OrderOut {
-        size_t sigma, yz, box;
-        int nch;
+        size_t sigma, yz, box, tbox;
+        int nch, ntl;
     };
     std::map<const HostGroup *, OrderOut> order_of;
     std::vector<const HostGroup *> to_order;
@@ -328,6 +328,9 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
         order_bytes += align16((size_t)dyz * N * 4);
         o.box = order_bytes;
         order_bytes += align16((size_t)dyz * o.nch * 8);
+        o.ntl = (N + 255) / 256;
+        o.tbox = order_bytes;
+        order_bytes += align16((size_t)dyz * o.ntl * 8);
         order_of[&g] = o;
         to_order.push_back(&g);
     }
@@ -468,6 +471,8 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
                 gd.yz = (const float *)(obase + oit->second.yz);
                 gd.box = (const float2 *)(obase + oit->second.box);
                 gd.n_chunks8 = oit->second.nch;
+                gd.tbox = (const float2 *)(obase + oit->second.tbox);
+                gd.n_tiles256 = oit->second.ntl;
             }
             gd.n_qtiles = (N + qsz - 1) / qsz;
             gd.n_mblocks = (gd.n_members + v.m - 1) / v.m;
@@ -500,6 +505,7 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
         J.sigma = (int *)(obase + o.sigma);
         J.yz = (float *)(obase + o.yz);
         J.box = (float2 *)(obase + o.box);
+        J.tbox = (float2 *)(obase + o.tbox);
         ojobs.push_back(J);
     }
     std::vector<ComposeJob> cjobs;

@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/te_ksg.h"
+#include "te_ksg.h"
 #include "ksg_internal.h"
 
 namespace teksg {
