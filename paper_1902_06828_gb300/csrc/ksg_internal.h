@@ -97,8 +97,7 @@ inline size_t ksg_lane_smem_bytes(int dyz, int jt)
 {
     const int warps = kLaneThreads / 32;
     return 4 * ((size_t)dyz * jt + 32 * (size_t)(jt + 4)) +
-           (size_t)warps * (2 * 4 * 8 * 4 + 4 * 4 * (size_t)dyz + 4 * (size_t)(jt / 64)) + 8 +
-           8 * (size_t)dyz * (jt / 8);
+           (size_t)warps * (2 * 4 * 8 * 4 + 4 * 4 * (size_t)dyz + 4 * (size_t)(jt / 64));
 }
 
 cudaError_t launch_ksg(const KsgLaunch &L, const KsgVariant &v, long long n_items, bool dx1,

@@ -549,7 +549,6 @@ __global__ void __launch_bounds__(QT) ksg_fused_kernel(const KsgLaunch L)
 constexpr int LQ = 4;            // query points per warp
 constexpr int LW = 8;            // warps per CTA
 constexpr int LQC = LQ * LW;     // query points per CTA
-constexpr int kMaxLaneChunks = 64;   // chunks of 8 per staged tile (tile <= 512 points)
 
 template <int KT>
 __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const KsgLaunch L)
@@ -582,16 +581,12 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
     float *s_dyz = s_dz + LW * LQ * 8;                    // [LW][LQ][8]
     float *s_q = s_dyz + LW * LQ * 8;                     // [LW][LQ][dyz]
     unsigned *s_bits = reinterpret_cast<unsigned *>(s_q + LW * LQ * dyz);  // [LW][wpt]
-    float2 *s_box = reinterpret_cast<float2 *>(
-        (reinterpret_cast<uintptr_t>(s_bits + LW * wpt) + 7) & ~(uintptr_t)7);  // [dyz][cpt]
     __shared__ const int32_t *s_mperm[32];
     __shared__ int s_mxoff[32];
     __shared__ int s_shared_perm;
     __shared__ int s_live[2][LW];
     __shared__ float s_bound[LW][LQ];
     __shared__ long long s_red[LW][32];
-    __shared__ int s_clist[kMaxLaneChunks];   // live chunks of the current tile
-    __shared__ int s_nlive;
     __shared__ float2 s_cqbox[32];
 
     // ---- this lane's member ----
@@ -637,13 +632,17 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
         }
     }
     __syncthreads();
-    // coarse test, taken identically by every thread: only values that no
-    // thread writes before the next barrier are read (s_bound, s_cqbox, tbox)
+    // Coarse test, taken identically by every thread without a barrier: it
+    // reads read-only data (tbox, s_cqbox) and `bound`, a register snapshot of
+    // the CTA's largest per-query bound taken right after a barrier.
     const bool coarse = sorted && jt == 256 && G.tbox != nullptr;
-    auto tile_dead = [&](int t, bool pass1) {
+    auto snapshot = [&]() {
+        float b = 0.f;
+        for (int e = 0; e < LW * LQ; ++e) b = fmaxf(b, (&s_bound[0][0])[e]);
+        return b;
+    };
+    auto tile_dead = [&](int t, bool pass1, float bound) {
         if (!coarse) return false;
-        float bound = 0.f;
-        for (int e = 0; e < LW * LQ; ++e) bound = fmaxf(bound, (&s_bound[0][0])[e]);
         float lb = 0.f;
         for (int d = pass1 ? 0 : dy; d < dyz; ++d) {
             const float2 b = G.tbox[(size_t)d * G.n_tiles256 + t];
@@ -655,39 +654,35 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
     const bool shared_perm = s_shared_perm != 0;
     const int32_t *perm0 = s_mperm[0];
 
-    // CTA-wide list of the tile's chunks that are live for some warp; every
-    // warp has written its bits before the barrier that precedes this call
-    auto build_list = [&]() {
-        if (warp == 0) {
-            int n = 0;
-            for (int c0 = 0; c0 < cpt; c0 += 32) {
-                const int c = c0 + lane;
-                unsigned any = 0;
-                if (c < cpt)
-                    for (int b = 0; b < LW; ++b)
-                        any |= (s_bits[b * wpt + (c >> 3)] >> (4 * (c & 7))) & 0xFu;
-                const unsigned mask = __ballot_sync(0xffffffffu, any != 0);
-                if (any) s_clist[n + __popc(mask & ((1u << lane) - 1u))] = c;
-                n += __popc(mask);
-            }
-            if (lane == 0) s_nlive = n;
-        }
-        __syncthreads();
+    // CTA-wide mask of the tile's chunks that are live for some warp, built
+    // by every warp from all warps' bits (identical in every warp; called
+    // between the liveness barrier and the staging barrier)
+    auto cta_mask = [&](int jn) {
+        const int nct = (jn + 7) >> 3;
+        unsigned any = 0;
+        if (lane < nct)
+            for (int b = 0; b < LW; ++b)
+                any |= (s_bits[b * wpt + (lane >> 3)] >> (4 * (lane & 7))) & 0xFu;
+        return __ballot_sync(0xffffffffu, any != 0);
     };
 
     // stage the live chunks: thread = (member m, point u) for X, (dim, point)
     // for Y and Z; four chunks per round keep several gathers in flight
-    auto stage = [&](int j0) {
-        const int nl = s_nlive;
+    auto stage = [&](int j0, unsigned mask) {
         const int m = tid >> 3, u = tid & 7;
         const int32_t *pm = shared_perm ? perm0 : s_mperm[m];
         const int xo = s_mxoff[m];
-        for (int r0 = 0; r0 < nl; r0 += 4) {
+        unsigned rest = mask;
+        while (rest) {
             float xv4[4], yz4[4];
             int cc[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                cc[q] = r0 + q < nl ? s_clist[r0 + q] : -1;
+                cc[q] = -1;
+                if (rest) {
+                    cc[q] = __ffs(rest) - 1;
+                    rest &= rest - 1;
+                }
                 xv4[q] = 0.f;
                 yz4[q] = 0.f;
                 if (cc[q] >= 0) {
@@ -711,16 +706,6 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
         }
     };
 
-    // the tile's chunk boxes, loaded once per CTA (sorted mode); callers
-    // synchronise before tile_live reads them
-    auto load_boxes = [&](int j0, int jn) {
-        const int nct = (jn + 7) >> 3;
-        for (int e = tid; e < dyz * nct; e += LW * 32) {
-            const int d = e / nct, c = e - d * nct;
-            s_box[d * cpt + c] = G.box[(size_t)d * G.n_chunks8 + (j0 >> 3) + c];
-        }
-    };
-
     // liveness of every (query, chunk) of the tile for this warp: bit 4c'+a of
     // word c/8; a lower bound (exact in float, rounding is monotone) on d_YZ
     // (pass 1) or d_Z (pass 2) below the query's bound keeps the chunk
@@ -735,9 +720,10 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
                     live = true;
                 } else {
                     const float *qc = s_q + (warp * LQ + a) * dyz;
+                    const int gc = (j0 >> 3) + c;
                     float lb = 0.f;
                     for (int d = pass1 ? 0 : dy; d < dyz; ++d) {
-                        const float2 b = s_box[d * cpt + c];
+                        const float2 b = __ldg(&G.box[(size_t)d * G.n_chunks8 + gc]);
                         const float q = qc[d];
                         lb = fmaxf(lb, fmaxf(fmaxf(__fsub_rn(b.x, q), __fsub_rn(q, b.y)), 0.f));
                     }
@@ -793,6 +779,7 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
         for (int b = 0; b < KB; ++b) buf[a][b] = CUDART_INF_F;
         thr[a] = CUDART_INF_F;
     }
+    float cbound = CUDART_INF_F;   // snapshot of the CTA's largest bound
     {
         const int home = sorted ? min((qtile * LQC) / jt, ntiles - 1) : 0;
         int up = home + 1, down = home - 1;
@@ -805,25 +792,25 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
             toggle = !toggle;
             const int j0 = t * jt;
             const int jn = min(jt, N - j0);
-            if (tile_dead(t, true)) continue;
-            if (sorted) {
-                load_boxes(j0, jn);
-                __syncthreads();
-            }
+            if (tile_dead(t, true, cbound)) continue;
             const bool live = tile_live(j0, jn, true);
             const int buf_i = nchk++ & 1;
             if (lane == 0) s_live[buf_i][warp] = live;
+            // Barrier: every warp has finished the previous tile (its compute and
+            // its bound updates) before anyone stages or snapshots.
             __syncthreads();
+            if (sorted) cbound = snapshot();
             int any = 0;
 #pragma unroll
             for (int b = 0; b < LW; ++b) any |= s_live[buf_i][b];
             if (!any) continue;
-            build_list();
-            stage(j0);
+            const unsigned mask = cta_mask(jn);
+            stage(j0, mask);
             __syncthreads();
-            const int nl = s_nlive;
-            for (int li = 0; li < nl; ++li) {
-                const int c = s_clist[li] * JC;
+            unsigned rest = mask;
+            while (rest) {
+                const int c = (__ffs(rest) - 1) * JC;
+                rest &= rest - 1;
                 const unsigned live4 = (s_bits[warp * wpt + (c >> 6)] >> (4 * ((c >> 3) & 7))) & 0xFu;
                 if (!live4) continue;
                 chunk_dist(j0, c, live4);
@@ -861,7 +848,6 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
                 }
                 __syncwarp();
             }
-            __syncthreads();
         }
     }
 
@@ -883,15 +869,14 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
         const float em = warp_max(eps[a]);
         if (lane == 0) s_bound[warp][a] = prune2 ? em : CUDART_INF_F;
     }
-    __syncthreads();   // every warp's pass-2 bounds before the coarse tile test
+    __syncthreads();   // every warp's pass-2 bounds before the snapshot
+    cbound = snapshot();
     for (int t = 0; t < ntiles; ++t) {
         const int j0 = t * jt;
         const int jn = min(jt, N - j0);
         bool live = true;
-        if (prune2 && tile_dead(t, false)) continue;
+        if (prune2 && tile_dead(t, false, cbound)) continue;
         if (prune2) {
-            load_boxes(j0, jn);
-            __syncthreads();
             live = tile_live(j0, jn, false);
         }
         else {
@@ -911,12 +896,13 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
 #pragma unroll
         for (int b = 0; b < LW; ++b) any |= s_live[buf_i][b];
         if (!any) continue;
-        build_list();
-        stage(j0);
+        const unsigned mask = cta_mask(jn);
+        stage(j0, mask);
         __syncthreads();
-        const int nl = s_nlive;
-        for (int li = 0; li < nl; ++li) {
-            const int c = s_clist[li] * JC;
+        unsigned rest = mask;
+        while (rest) {
+            const int c = (__ffs(rest) - 1) * JC;
+            rest &= rest - 1;
             const unsigned live4 = (s_bits[warp * wpt + (c >> 6)] >> (4 * ((c >> 3) & 7))) & 0xFu;
             if (!live4) continue;
             chunk_dist(j0, c, live4);
@@ -936,7 +922,6 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
             }
             __syncwarp();
         }
-        __syncthreads();
     }
 
     // ---------------- work counters, digamma key ----------------
