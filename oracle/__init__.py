@@ -5,4 +5,4 @@ CPU-baseline / reference leg are the only code allowed to import it.  The
 product library (paper_1902_06828_gb300) never imports, links or calls it.
 The oracle is independent of the CUDA path: it shares no code with it.
 """
-from . import ksg, network  # noqa: F401
+from . import gauss, ksg, network  # noqa: F401

@@ -311,3 +311,63 @@ def test_greedy_recovers_chain():
     np.testing.assert_array_equal(adj, w["adj"])
     lags = {(src, r.target): lag for r in res for src, lag in r.sel_sources}
     assert lags == {(0, 1): 1, (1, 2): 1}
+
+
+# ---- linear-Gaussian estimator ------------------------------------------------
+
+def _resid_var(target, regressors):
+    """Residual variance of least squares with an intercept (numpy lstsq)."""
+    A = np.column_stack([np.ones(len(target))] + list(regressors))
+    coef, *_ = np.linalg.lstsq(A, target, rcond=None)
+    r = target - A @ coef
+    return float(r @ r)
+
+
+def test_gauss_equals_regression_residual_identity():
+    """For 1-D X and Y: I(X;Y|Z) = 1/2 ln(var(Y | Z) / var(Y | X, Z)), the
+    Granger form, computed here by least squares instead of determinants."""
+    from oracle import gauss
+    w = synth.workload_chain3(T=800, seed=5)
+    s = w["series"].astype(np.float64)
+    N = s.shape[1] - 2
+    Y = s[2, 2:]
+    X = s[1, 1:-1]
+    Z = [s[2, 1:-1], s[2, 0:-2]]
+    want = 0.5 * np.log(_resid_var(Y, Z) / _resid_var(Y, [X] + Z))
+    got = gauss.cmi_gauss(w["series"], w["x"], w["y"], w["z"], max_lag=2)[0]
+    assert abs(got - want) < 1e-12
+    # empty Z: mutual information 1/2 ln(var(Y) / var(Y | X)) = -1/2 ln(1 - r^2)
+    r = np.corrcoef(X, Y)[0, 1]
+    got0 = gauss.cmi_gauss(w["series"], w["x"], w["y"], [], max_lag=2)[0]
+    assert abs(got0 + 0.5 * np.log(1 - r * r)) < 1e-12
+
+
+def test_gauss_symmetry_affine_and_identity_permutation():
+    from oracle import gauss
+    w = synth.workload_chain3(T=500, seed=6)
+    s = w["series"]
+    a = gauss.cmi_gauss(s, w["x"], w["y"], w["z"], max_lag=2)[0]
+    b = gauss.cmi_gauss(s, w["y"], w["x"], w["z"], max_lag=2)[0]
+    s2 = s.copy()
+    s2[1] = s[1] * np.float32(4.0)           # exact in float32
+    c = gauss.cmi_gauss(s2, w["x"], w["y"], w["z"], max_lag=2)[0]
+    s3 = s.copy()
+    s3[1] = s[1] + np.float32(3.0)           # rounds the data at float32 ulp
+    e = gauss.cmi_gauss(s3, w["x"], w["y"], w["z"], max_lag=2)[0]
+    assert abs(a - e) < 1e-7
+    N = s.shape[1] - 2
+    d = gauss.cmi_gauss(s, w["x"], w["y"], w["z"], max_lag=2,
+                        perms=np.arange(N)[None, :])
+    assert abs(a - b) < 1e-12 and abs(a - c) < 1e-12 and abs(d[1] - a) < 1e-15
+
+
+def test_gauss_population_closed_form():
+    from oracle import gauss
+    vals = []
+    cov = None
+    for seed in range(8):
+        x, cov = synth.gaussian_cmi_data(20000, seed)
+        vals.append(gauss.cmi_gauss(x.astype(np.float32), [(0, 0)], [(1, 0)], [(2, 0)],
+                                    max_lag=0)[0])
+    want = _gauss_cmi_closed(cov)
+    assert abs(np.mean(vals) - want) < 3 * np.std(vals, ddof=1) / math.sqrt(len(vals)) + 2e-4
