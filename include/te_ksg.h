@@ -158,6 +158,28 @@ typedef struct {
 te_status cmi_ksg_batch(te_ctx *ctx, const te_cmi_job *jobs, int32_t n_jobs, double *out,
                         int64_t *out_key);
 
+/* ---- linear-Gaussian estimate ----------------------------------------------
+ *
+ * cmi_gauss: the Gaussian (linear) CMI estimate used by the paper for its VAR
+ * networks (Methods, Vector autoregressive process; transfer entropy equals
+ * Granger causality for Gaussian variables).  The paper prints no formula; the
+ * reading used is the plug-in estimate from the sample covariance (ddof = 1) of
+ * the embedded variables,
+ *   I(X;Y|Z) = 1/2 [ln|S_XZ| + ln|S_YZ| - ln|S_Z| - ln|S_XYZ|]   (|S_Z| = 1 if
+ * dz = 0), evaluated as 1/2 [ln|Schur_X given Z| - ln|Schur_X given (Y,Z)|] with
+ * FP64 Cholesky factors.  Surrogate s permutes the rows of the whole X block
+ * with the same permutation cmi_ksg uses (seed, stream_tag, s); Y and Z are
+ * never permuted.  params: max_lag, n_surr, seed, stream_tag are used; k and
+ * theiler are ignored.  dx <= 8, dx + dy + dz <= TE_MAX_DIMS, N > dx+dy+dz+1.
+ * out_cmi: host double[1 + S]; out_err_bound: NULL or host double[1 + S], a
+ * first-order bound on |out_cmi - exact FP64 plug-in value| from the error
+ * model of the cross-covariance contraction.
+ * Errors: TE_EINVAL (as cmi_ksg, dx > 8, too few points, a singular
+ * conditioning covariance), TE_ENOMEM, TE_ECUDA. */
+te_status cmi_gauss(te_ctx *ctx, const te_data *data, const te_var *x, int32_t dx,
+                    const te_var *y, int32_t dy, const te_var *z, int32_t dz,
+                    const te_ksg_params *params, double *out_cmi, double *out_err_bound);
+
 /* ---- greedy network inference -------------------------------------------- */
 
 typedef struct {

@@ -26,7 +26,7 @@ from ._abi import TE_MAX_DIMS, TE_MAX_K  # noqa: F401
 
 __all__ = ["Context", "Data", "TEError", "te_data_create", "cmi_ksg", "cmi_ksg_debug",
            "cmi_ksg_batch", "te_network_infer", "te_get_stats", "Job", "library_path",
-           "cmi_ksg_static", "te_serve_start", "te_serve_submit", "te_serve_poll",
+           "cmi_ksg_static", "cmi_gauss", "te_serve_start", "te_serve_submit", "te_serve_poll",
            "te_serve_cancel", "te_serve_stop", "te_serve_get_stats"]
 
 
@@ -179,6 +179,24 @@ def cmi_ksg(ctx: Context, data: Data, x, y, z=(), *, k=4, theiler=0, max_lag=Non
     if return_keys:
         return out, _keys_to_int(keys)
     return out
+
+
+def cmi_gauss(ctx: Context, data: Data, x, y, z=(), *, max_lag=None, n_surr=0, seed=0,
+              stream_tag=0):
+    """Linear-Gaussian CMI and n_surr permutation surrogates -> (values, error
+    bounds), each float64 [1 + n_surr]."""
+    if max_lag is None:
+        max_lag = _default_max_lag(x, y, z)
+    xv, dx = _vars(x)
+    yv, dy = _vars(y)
+    zv, dz = _vars(z)
+    out = np.zeros(1 + max(int(n_surr), 0), np.float64)
+    err = np.zeros_like(out)
+    p = _params(1, 0, max_lag, n_surr, seed, stream_tag)
+    st = ctx._lib.cmi_gauss(ctx._h, data._h, xv, dx, yv, dy, zv if dz else None, dz, C.byref(p),
+                            out.ctypes.data, err.ctypes.data)
+    _check(ctx._h, st)
+    return out, err
 
 
 def _keys_to_int(keys):

@@ -92,6 +92,8 @@ SIGNATURES = {
                                 C.POINTER(TeVar), _I32, C.POINTER(KsgParams), _I32, _P, _P, _P,
                                 _P]),
     "cmi_ksg_batch": (C.c_int, [_P, C.POINTER(CmiJob), _I32, _P, _P]),
+    "cmi_gauss": (C.c_int, [_P, _P, C.POINTER(TeVar), _I32, C.POINTER(TeVar), _I32,
+                            C.POINTER(TeVar), _I32, C.POINTER(KsgParams), _P, _P]),
     "te_network_infer": (C.c_int, [_P, _P, C.POINTER(InferParams),
                                    C.POINTER(C.POINTER(NetworkResult))]),
     "te_network_result_free": (None, [C.POINTER(NetworkResult)]),

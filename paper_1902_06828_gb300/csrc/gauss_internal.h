@@ -1,0 +1,35 @@
+// Internal interface of the linear-Gaussian CMI kernels (not public).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace teksg {
+
+constexpr int kGaussMaxDims = 32;   // dx + dy + dz
+constexpr int kGaussMaxX = 8;       // dx
+
+// Columns are X (dx), then Y (dy), then Z; W = (Y, Z) has dw = dy + dz
+// columns.  The value of column c at point t is base[cols[c] + t].
+struct GaussArgs {
+    const float *base;
+    const int *cols;        // [d] device
+    int N, S, dx, dy, dw, d;
+    const int32_t *perms;   // [S][N] surrogate permutations of the rows of X
+    double *mean;           // [d]
+    double *cov;            // [d][d] sample covariance, ddof = 1
+    double *LW, *LZ;        // [dw][dw] lower Cholesky factors of S_WW and S_ZZ
+    double *norms;          // ||L_W^-1||_F^2, ||L_Z^-1||_F^2
+    double *scratch;        // [kGaussMaxDims]
+    int *status;            // [0] 1: a fixed block is not positive definite;
+                            // [1] 1: a tensor-core wait timed out
+    double *cross;          // [S + 1][dx][dw] cross-covariance of permuted X with W
+    double *out, *err;      // [S + 1] estimates and error bounds
+};
+
+cudaError_t gauss_launch_stats(const GaussArgs &A, cudaStream_t st);
+cudaError_t gauss_launch_cross_tc(const GaussArgs &A, cudaStream_t st);
+double gauss_tc_gamma();   // relative error factor of the tensor-core contraction
+cudaError_t gauss_launch_schur(const GaussArgs &A, double gamma, cudaStream_t st);
+
+}  // namespace teksg

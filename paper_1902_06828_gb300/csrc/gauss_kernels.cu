@@ -1,0 +1,456 @@
+// Linear-Gaussian CMI (cmi_gauss) kernels.
+//
+// Plug-in estimate from the sample covariance (ddof = 1) of the embedded
+// variables (Methods, Vector autoregressive process: the Gaussian estimator;
+// transfer entropy equals Granger causality for Gaussian variables):
+//   I(X;Y|Z) = 1/2 [ln|S_XZ| + ln|S_YZ| - ln|S_Z| - ln|S_XYZ|]
+//            = 1/2 [ln|Schur_X|Z| - ln|Schur_X|W|],   W = (Y, Z),
+// with Schur_X|V = S_XX - S_XV S_VV^-1 S_VX.  S_XX, S_ZZ and S_WW do not
+// depend on the surrogate (a permutation of the rows of X leaves S_XX
+// unchanged), so they are formed and factored once in FP64; each surrogate
+// only needs its cross-covariance S_XW, a contraction over the N points.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include <cmath>
+
+#include "gauss_internal.h"
+
+namespace teksg {
+
+namespace {
+
+__device__ __forceinline__ double block_sum(double v, double *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int a = 0; a < (int)(blockDim.x >> 5); ++a) s += red[a];
+    __syncthreads();
+    return s;   // valid in thread 0
+}
+
+// column means: block d
+__global__ void gauss_mean_kernel(GaussArgs A)
+{
+    __shared__ double red[32];
+    const int d = blockIdx.x;
+    const float *col = A.base + A.cols[d];
+    double s = 0.0;
+    for (int t = threadIdx.x; t < A.N; t += blockDim.x) s += (double)col[t];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) A.mean[d] = s / (double)A.N;
+}
+
+// covariance of columns (i, j), i <= j: block = pair index
+__global__ void gauss_cov_kernel(GaussArgs A)
+{
+    __shared__ double red[32];
+    int p = blockIdx.x, i = 0;
+    while (p >= A.d - i) {
+        p -= A.d - i;
+        ++i;
+    }
+    const int j = i + p;
+    const float *ci = A.base + A.cols[i];
+    const float *cj = A.base + A.cols[j];
+    const double mi = A.mean[i], mj = A.mean[j];
+    double s = 0.0;
+    for (int t = threadIdx.x; t < A.N; t += blockDim.x)
+        s += ((double)ci[t] - mi) * ((double)cj[t] - mj);
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) {
+        const double c = s / (double)(A.N - 1);
+        A.cov[i * A.d + j] = c;
+        A.cov[j * A.d + i] = c;
+    }
+}
+
+// In-place FP64 Cholesky of an n x n SPD matrix (row-major, lower factor);
+// returns false if a pivot is not positive.
+__device__ bool chol(double *a, int n, int ld)
+{
+    for (int j = 0; j < n; ++j) {
+        double s = a[j * ld + j];
+        for (int k = 0; k < j; ++k) s -= a[j * ld + k] * a[j * ld + k];
+        if (!(s > 0.0)) return false;
+        const double l = sqrt(s);
+        a[j * ld + j] = l;
+        for (int i = j + 1; i < n; ++i) {
+            double t = a[i * ld + j];
+            for (int k = 0; k < j; ++k) t -= a[i * ld + k] * a[j * ld + k];
+            a[i * ld + j] = t / l;
+        }
+    }
+    return true;
+}
+
+// ||L^-1||_F^2 for lower-triangular L (n x n): sum of squares of the inverse
+__device__ double inv_frob2(const double *L, int n, int ld, double *col)
+{
+    double s = 0.0;
+    for (int c = 0; c < n; ++c) {
+        for (int i = 0; i < n; ++i) {
+            double t = (i == c) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) t -= L[i * ld + k] * col[k];
+            col[i] = i < c ? 0.0 : t / L[i * ld + i];
+            s += col[i] * col[i];
+        }
+    }
+    return s;
+}
+
+// Factor S_ZZ and S_WW (single thread).  W = the Y then Z columns; Z is the
+// trailing block of W.  Writes L_W, L_Z (lower, row-major, ld = dw) and
+// ||L^-1||_F^2 of each; status[0] = 1 if a block is not positive definite.
+__global__ void gauss_factor_kernel(GaussArgs A)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int dx = A.dx, dw = A.dw, dy = A.dy, dz = dw - dy, d = A.d;
+    for (int r = 0; r < dw; ++r)
+        for (int c = 0; c < dw; ++c) {
+            A.LW[r * dw + c] = c <= r ? A.cov[(dx + r) * d + dx + c] : 0.0;
+            if (r < dz && c < dz) A.LZ[r * dw + c] = c <= r ? A.cov[(dx + dy + r) * d + dx + dy + c] : 0.0;
+        }
+    bool ok = chol(A.LW, dw, dw);
+    if (dz > 0) ok = ok && chol(A.LZ, dz, dw);
+    A.status[0] = ok ? 0 : 1;
+    if (!ok) return;
+    A.norms[0] = inv_frob2(A.LW, dw, dw, A.scratch);
+    A.norms[1] = dz > 0 ? inv_frob2(A.LZ, dz, dw, A.scratch) : 0.0;
+}
+
+// Per surrogate (one thread): Schur complements given Z and given W, their
+// log-determinants, the estimate and a first-order bound on its error from
+// the cross-covariance error model |dS_XW_ij| <= gamma sqrt(S_ii S_jj).
+__global__ void gauss_schur_kernel(GaussArgs A, double gamma)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s > A.S) return;
+    const int dx = A.dx, dw = A.dw, dy = A.dy, dz = dw - dy, d = A.d;
+    const double *c = A.cross + (size_t)s * dx * dw;   // [dx][dw]
+    double v[kGaussMaxDims], Sm[kGaussMaxX * kGaussMaxX], tmp[kGaussMaxDims];
+    double ld[2], bound[2];
+    for (int which = 0; which < 2; ++which) {
+        // which 0: given Z (trailing dz entries of W); 1: given W
+        const int n = which == 0 ? dz : dw;
+        const int off = which == 0 ? dy : 0;
+        const double *L = which == 0 ? A.LZ : A.LW;
+        // Sm = S_XX - V^T V, V = L^-1 C_V  (column per x dim)
+        for (int a = 0; a < dx; ++a)
+            for (int b = 0; b < dx; ++b) Sm[a * dx + b] = A.cov[a * d + b];
+        double vnorm2 = 0.0, dcnorm2 = 0.0;
+        double vall[kGaussMaxX * kGaussMaxDims];
+        for (int a = 0; a < dx; ++a) {
+            for (int r = 0; r < n; ++r) {
+                double t = c[a * dw + off + r];
+                for (int k = 0; k < r; ++k) t -= L[r * dw + k] * v[k];
+                v[r] = t / L[r * dw + r];
+                vnorm2 += v[r] * v[r];
+                const double e = gamma * sqrt(A.cov[a * d + a] *
+                                              A.cov[(dx + off + r) * d + dx + off + r]);
+                dcnorm2 += e * e;
+            }
+            for (int r = 0; r < n; ++r) vall[a * kGaussMaxDims + r] = v[r];
+        }
+        for (int a = 0; a < dx; ++a)
+            for (int b = 0; b < dx; ++b) {
+                double t = 0.0;
+                for (int r = 0; r < n; ++r) t += vall[a * kGaussMaxDims + r] * vall[b * kGaussMaxDims + r];
+                Sm[a * dx + b] -= t;
+            }
+        if (!chol(Sm, dx, dx)) {
+            ld[which] = CUDART_NAN;
+            bound[which] = CUDART_INF;
+            continue;
+        }
+        double l = 0.0;
+        for (int a = 0; a < dx; ++a) l += 2.0 * log(Sm[a * dx + a]);
+        ld[which] = l;
+        // d ln|Sm| <= ||Sm^-1||_F ||dSm||_F,  ||dSm||_F <= 2 ||dC||_F ||L^-1||_F ||V||_F
+        const double sinv = sqrt(inv_frob2(Sm, dx, dx, tmp));
+        const double linv = n > 0 ? sqrt(A.norms[which == 0 ? 1 : 0]) : 0.0;
+        bound[which] = sinv * 2.0 * sqrt(dcnorm2) * linv * sqrt(vnorm2);
+    }
+    A.out[s] = 0.5 * (ld[0] - ld[1]);
+    // factor 2 for second-order terms
+    A.err[s] = 2.0 * 0.5 * (bound[0] + bound[1]);
+}
+
+// ---------------- tensor-core cross-covariance (tcgen05, split TF32) ----------------
+// D[m][n] = sum_t A[m][t] B[n][t] with A[m][t] = x_i(pi_s(t)) - mean_i (row m =
+// (surrogate s, X dim i)) and B[n][t] = w_n(t) - mean_n (n < dw, zero above).
+// Each operand is split in two TF32 parts, a = a_hi + a_lo (centred in FP64,
+// a_hi = tf32(a), a_lo = tf32(a - a_hi)); the product is a_hi b_hi + a_hi b_lo +
+// a_lo b_hi, three tcgen05.mma.kind::tf32 per K step, FP32 accumulation in
+// tensor memory.  Every kGaussGroup chunks of 32 points the 128 x 32 FP32
+// accumulator is read back (tcgen05.ld) and added to FP64 registers, which
+// bounds the FP32 accumulation error.  One CTA (4 warps) per 128 rows; one
+// thread issues the MMAs, the others stage operands.  Operands use the
+// canonical K-major layout without swizzle: 8-row x 16-byte core matrices,
+// K-adjacent core matrices 128 bytes apart (leading byte offset), 8-row groups
+// 1024 bytes apart (stride byte offset).
+constexpr int kGaussTileM = 128;
+constexpr int kGaussTileN = 32;
+constexpr int kGaussKC = 32;                     // points per chunk (128 bytes of TF32)
+constexpr int kGaussGroup = 4;                   // chunks per FP32 accumulation group
+constexpr unsigned kGaussSpinLimit = 1u << 26;   // bounded mbarrier waits
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float f)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
+    return r;
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1u << 46;   // descriptor version for this architecture
+    // base offset 0, absolute LBO mode 0, layout type 0 = no swizzle
+    return d;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity)
+{
+    for (unsigned it = 0; it < kGaussSpinLimit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int a = 0; a < 32; ++a) v[a] = __uint_as_float(r[a]);
+}
+
+// byte offset of element (row, k) of a K-major no-swizzle tile with 8 core
+// matrices (32 TF32 values) per row group
+__device__ __forceinline__ uint32_t cm_offset(int row, int k)
+{
+    return (uint32_t)(((row >> 3) * 8 + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+__global__ void __launch_bounds__(128, 1) gauss_cross_tc_kernel(GaussArgs A)
+{
+    __shared__ __align__(1024) uint32_t sA_hi[kGaussTileM * kGaussKC];
+    __shared__ __align__(1024) uint32_t sA_lo[kGaussTileM * kGaussKC];
+    __shared__ __align__(1024) uint32_t sB_hi[kGaussTileN * kGaussKC];
+    __shared__ __align__(1024) uint32_t sB_lo[kGaussTileN * kGaussKC];
+    __shared__ __align__(8) unsigned long long s_mbar;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fail;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int rows = (A.S + 1) * A.dx;
+    const int m = blockIdx.x * kGaussTileM + tid;   // this thread's row
+    const bool mvalid = m < rows;
+    const int ms = mvalid ? m / A.dx : 0, mi = mvalid ? m % A.dx : 0;
+    const int32_t *perm = (mvalid && ms > 0) ? A.perms + (size_t)(ms - 1) * A.N : nullptr;
+    const float *cx = A.base + A.cols[mi];
+    const double mx = A.mean[mi];
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"((uint32_t)kGaussTileN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) |
+                           ((uint32_t)(kGaussTileN >> 3) << 17) |
+                           ((uint32_t)(kGaussTileM >> 4) << 24);
+    const uint32_t aHi = smem_u32(sA_hi), aLo = smem_u32(sA_lo);
+    const uint32_t bHi = smem_u32(sB_hi), bLo = smem_u32(sB_lo);
+    const uint32_t mbar = smem_u32(&s_mbar);
+
+    double acc[kGaussTileN];
+#pragma unroll
+    for (int a = 0; a < kGaussTileN; ++a) acc[a] = 0.0;
+    uint32_t phase = 0;
+    const int nchunks = (A.N + kGaussKC - 1) / kGaussKC;
+    bool failed = false;
+
+    for (int ch = 0; ch < nchunks && !failed; ++ch) {
+        const int k0 = ch * kGaussKC;
+        // stage A: this thread's row, 32 points
+        {
+            unsigned char *hb = reinterpret_cast<unsigned char *>(sA_hi);
+            unsigned char *lb = reinterpret_cast<unsigned char *>(sA_lo);
+#pragma unroll 4
+            for (int k = 0; k < kGaussKC; ++k) {
+                const int t = k0 + k;
+                float hi = 0.f, lo = 0.f;
+                if (mvalid && t < A.N) {
+                    const int tx = perm ? perm[t] : t;
+                    const double v = (double)cx[tx] - mx;
+                    const uint32_t h = to_tf32((float)v);
+                    hi = __uint_as_float(h);
+                    lo = __uint_as_float(to_tf32((float)(v - (double)hi)));
+                }
+                const uint32_t off = cm_offset(tid, k);
+                *reinterpret_cast<float *>(hb + off) = hi;
+                *reinterpret_cast<float *>(lb + off) = lo;
+            }
+        }
+        // stage B: 32 rows x 32 points, 8 values per thread
+        {
+            unsigned char *hb = reinterpret_cast<unsigned char *>(sB_hi);
+            unsigned char *lb = reinterpret_cast<unsigned char *>(sB_lo);
+            for (int e = tid; e < kGaussTileN * kGaussKC; e += 128) {
+                const int n = e / kGaussKC, k = e % kGaussKC;
+                const int t = k0 + k;
+                float hi = 0.f, lo = 0.f;
+                if (n < A.dw && t < A.N) {
+                    const double v = (double)A.base[A.cols[A.dx + n] + t] - A.mean[A.dx + n];
+                    hi = __uint_as_float(to_tf32((float)v));
+                    lo = __uint_as_float(to_tf32((float)(v - (double)hi)));
+                }
+                const uint32_t off = cm_offset(n, k);
+                *reinterpret_cast<float *>(hb + off) = hi;
+                *reinterpret_cast<float *>(lb + off) = lo;
+            }
+        }
+        // generic-proxy smem writes -> visible to the tensor core (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const bool first = (ch % kGaussGroup) == 0;
+#pragma unroll
+            for (int q = 0; q < kGaussKC / 8; ++q) {   // K = 8 TF32 per MMA
+                const uint32_t ko = q * 256;            // two core matrices along K
+                const uint64_t dAh = smem_desc(aHi + ko, 128, 1024);
+                const uint64_t dAl = smem_desc(aLo + ko, 128, 1024);
+                const uint64_t dBh = smem_desc(bHi + ko, 128, 1024);
+                const uint64_t dBl = smem_desc(bLo + ko, 128, 1024);
+                mma_tf32(tmem, dAh, dBh, idesc, (first && q == 0) ? 0u : 1u);
+                mma_tf32(tmem, dAh, dBl, idesc, 1u);
+                mma_tf32(tmem, dAl, dBh, idesc, 1u);
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    mbar)
+                : "memory");
+        }
+        // every thread waits: the MMAs have read the smem tiles (and, at a
+        // group end, written the accumulator) before they are reused
+        if (!mbar_wait(mbar, phase)) atomicExch(&s_fail, 1);
+        __syncthreads();
+        if (s_fail) {
+            // give the in-flight MMAs a second bounded wait before the
+            // accumulator is freed; report the failure either way
+            mbar_wait(mbar, phase);
+            failed = true;
+            break;
+        }
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const bool group_end = (ch % kGaussGroup) == kGaussGroup - 1 || ch == nchunks - 1;
+        if (group_end) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+#pragma unroll
+            for (int a = 0; a < kGaussTileN; ++a) acc[a] += (double)v[a];
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        }
+        __syncthreads();
+    }
+    if (failed && tid == 0) atomicExch(A.status + 1, 1);
+    if (!failed && mvalid) {
+        const double inv = 1.0 / (double)(A.N - 1);
+#pragma unroll
+        for (int n = 0; n < kGaussTileN; ++n)
+            if (n < A.dw) A.cross[(size_t)m * A.dw + n] = acc[n] * inv;
+    }
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"((uint32_t)kGaussTileN));
+}
+
+}  // namespace
+
+cudaError_t gauss_launch_stats(const GaussArgs &A, cudaStream_t st)
+{
+    gauss_mean_kernel<<<A.d, 256, 0, st>>>(A);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    gauss_cov_kernel<<<A.d * (A.d + 1) / 2, 256, 0, st>>>(A);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    gauss_factor_kernel<<<1, 32, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t gauss_launch_cross_tc(const GaussArgs &A, cudaStream_t st)
+{
+    const int rows = (A.S + 1) * A.dx;
+    gauss_cross_tc_kernel<<<(rows + kGaussTileM - 1) / kGaussTileM, 128, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
+double gauss_tc_gamma()
+{
+    // split products: 3 * 2^-22 relative; FP32 accumulation of at most
+    // 3 * kGaussKC * kGaussGroup products per group, 2^-23 per addition
+    return 3.0 * std::ldexp(1.0, -22) + 3.0 * kGaussKC * kGaussGroup * std::ldexp(1.0, -23);
+}
+
+cudaError_t gauss_launch_schur(const GaussArgs &A, double gamma, cudaStream_t st)
+{
+    gauss_schur_kernel<<<(A.S + 1 + 63) / 64, 64, 0, st>>>(A, gamma);
+    return cudaGetLastError();
+}
+
+}  // namespace teksg

@@ -655,7 +655,7 @@ void te_ctx_destroy(te_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     DevBuf *bufs[] = {&ctx->ws_groups, &ctx->ws_members, &ctx->ws_cols,  &ctx->ws_acc,
                       &ctx->ws_keys,   &ctx->ws_perm,    &ctx->ws_stat,  &ctx->ws_dbg,
-                      &ctx->ws_order,  &ctx->ws_ojobs,  &ctx->ws_cperm};
+                      &ctx->ws_order,  &ctx->ws_ojobs,  &ctx->ws_cperm, &ctx->ws_gauss};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->q_dev) cudaFree(ctx->q_dev);

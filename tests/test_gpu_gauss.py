@@ -1,0 +1,51 @@
+"""cmi_gauss against the FP64 oracle: every value within the error bound the
+library reports for it (plus FP64 rounding noise)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import gauss as ogauss
+from oracle import ksg as oksg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import paper_1902_06828_gb300 as te
+    ctx = te.Context(0)
+    yield te, ctx
+    ctx.close()
+
+
+CASES = [
+    ("chain3", [(1, 1)], [(2, 0)], [(2, 1), (2, 2)], 2, 50),
+    ("chain3", [(1, 1)], [(2, 0)], [], 2, 30),                                  # empty Z
+    ("chain3", [(0, 1), (1, 1), (1, 2)], [(2, 0)], [(2, 1)], 2, 20),            # dx = 3
+    ("var10", [(3, 2)], [(0, 0)], [(0, 1), (0, 2), (4, 1)], 5, 100),
+    ("var10", [(9, 2)], [(0, 0), (1, 0)], [(0, 1)] + [(q, 1) for q in range(2, 9)], 5, 40),
+]
+
+
+@pytest.mark.parametrize("wl,x,y,z,ml,S", CASES)
+def test_gauss_matches_oracle_within_reported_bound(env, wl, x, y, z, ml, S):
+    te, ctx = env
+    s = (synth.workload_chain3(T=1000, seed=2)["series"] if wl == "chain3"
+         else synth.workload_var10(T=10000, seed=1)["series"])
+    data = te.te_data_create(ctx, s)
+    got, err = te.cmi_gauss(ctx, data, x, y, z, max_lag=ml, n_surr=S, seed=4, stream_tag=8)
+    N = s.shape[1] - ml
+    perms = np.stack([oksg.permutation(4, 8, 0, 0, k, N) for k in range(1, S + 1)])
+    want = ogauss.cmi_gauss(s, x, y, z, max_lag=ml, perms=perms)
+    assert np.all(np.isfinite(got)) and np.all(err >= 0)
+    assert np.all(np.abs(got - want) <= err + 1e-12), np.max(np.abs(got - want) - err)
+    # measured accuracy of the split-TF32 contraction is far inside the bound
+    assert np.max(np.abs(got - want)) < 1e-7
+
+
+def test_gauss_singular_conditioning_rejected(env):
+    te, ctx = env
+    s = synth.workload_chain3(T=300, seed=1)["series"]
+    data = te.te_data_create(ctx, s)
+    with pytest.raises(te.TEError, match="singular"):
+        te.cmi_gauss(ctx, data, [(1, 1)], [(2, 0)], [(2, 1), (2, 1)], max_lag=2)
