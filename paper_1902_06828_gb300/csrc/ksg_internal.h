@@ -33,6 +33,9 @@ struct GroupDesc {
     int n_chunks8;
     const float2 *tbox;     // [dy + dz][n_tiles256]: (min, max) per aligned 256-point tile
     int n_tiles256;
+    // Empty Z, one Y and one X variable, no Theiler window: the Y column sorted
+    // ascending (else nullptr).  Counts then reduce to 1-D range counts.
+    const float *ysorted;
 };
 
 // One spatial-order job (one CTA): Morton keys of the (Y, Z) coordinates of a
@@ -63,7 +66,16 @@ struct MemberDesc {
                             // time index of X)
     int xcol;               // first index into cols[] of the dx X column offsets
     int out;                // output slot
+    const float *xsorted;   // the X column sorted ascending when the group has ysorted
 };
+
+// Sort N floats ascending (one CTA per job, N <= kMaxOrderN).
+struct ValueSortJob {
+    const float *src;
+    float *dst;
+    int N;
+};
+cudaError_t launch_value_sort(const ValueSortJob *jobs, int n_jobs, cudaStream_t st);
 
 // A column is addressed as base + off: the value of the column at point i is
 // base[off + i], off = proc * T + max_lag - lag.

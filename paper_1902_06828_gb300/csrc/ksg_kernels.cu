@@ -537,6 +537,29 @@ __global__ void __launch_bounds__(QT) ksg_fused_kernel(const KsgLaunch L)
     }
 }
 
+// Number of u with |fl(col[u] - x)| < e over an ascending column: fl(col[u]-x)
+// is non-decreasing in u (rounding is monotone), so the set is a contiguous
+// run found by two binary searches with exactly the pairwise predicate.
+__device__ __forceinline__ int range_count(const float *__restrict__ col, int n, float x, float e)
+{
+    int lo = 0, hi = n;   // first u with fl(col[u] - x) >= e
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__fsub_rn(__ldg(col + mid), x) >= e) hi = mid;
+        else lo = mid + 1;
+    }
+    const int a = lo;
+    lo = 0;
+    hi = n;               // first u with fl(col[u] - x) > -e
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__fsub_rn(__ldg(col + mid), x) > -e) hi = mid;
+        else lo = mid + 1;
+    }
+    return a - lo;
+}
+
+
 // ---------------- member-lane kernel ----------------
 // ksg_lane_kernel -- for single-variable X (every candidate of the greedy
 // steps).  Lanes are members: a CTA owns 32 members (one per lane) and 32
@@ -871,7 +894,22 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
     }
     __syncthreads();   // every warp's pass-2 bounds before the snapshot
     cbound = snapshot();
-    for (int t = 0; t < ntiles; ++t) {
+    // Empty Z with one X and one Y variable and no Theiler window: n_z = N - 1
+    // and n_xz, n_yz are 1-D range counts.  The member's X values over the
+    // points are the column's values (a permutation only reorders them), so
+    // both counts come from sorted columns, minus the point itself (distance 0
+    // counts iff eps > 0).  Exactly the counts of the pairwise loop below.
+    if (G.ysorted) {
+#pragma unroll
+        for (int a = 0; a < LQ; ++a) {
+            const float e = eps[a];
+            const int self = e > 0.f ? 1 : 0;
+            cz[a] = (float)(N - 1);
+            cxz[a] = (float)(range_count(md.xsorted, N, xi[a], e) - self);
+            cyz[a] = (float)(range_count(G.ysorted, N, s_q[(warp * LQ + a) * dyz], e) - self);
+        }
+    }
+    for (int t = 0; t < (G.ysorted ? 0 : ntiles); ++t) {
         const int j0 = t * jt;
         const int jn = min(jt, N - j0);
         bool live = true;
@@ -1113,6 +1151,33 @@ __global__ void __launch_bounds__(1024) order_kernel(const OrderJob *jobs)
     }
 }
 
+// Ascending sort of one column (bitonic in shared memory; +inf pads).
+__global__ void __launch_bounds__(1024) value_sort_kernel(const ValueSortJob *jobs)
+{
+    extern __shared__ float sv[];
+    const ValueSortJob J = jobs[blockIdx.x];
+    int P2 = 1;
+    while (P2 < J.N) P2 <<= 1;
+    for (int p = threadIdx.x; p < P2; p += blockDim.x) sv[p] = p < J.N ? J.src[p] : CUDART_INF_F;
+    __syncthreads();
+    for (int kk = 2; kk <= P2; kk <<= 1) {
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int t = threadIdx.x; t < (P2 >> 1); t += blockDim.x) {
+                const int lo = 2 * jj * (t / jj) + (t % jj);
+                const int hi = lo + jj;
+                const bool up = (lo & kk) == 0;
+                const float x = sv[lo], y = sv[hi];
+                if ((x > y) == up) {
+                    sv[lo] = y;
+                    sv[hi] = x;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int p = threadIdx.x; p < J.N; p += blockDim.x) J.dst[p] = sv[p];
+}
+
 // out[p] = perm[sigma[p]]: a surrogate permutation composed with a group's
 // spatial order (index arrays only; the data is never copied)
 __global__ void compose_kernel(const ComposeJob *jobs)
@@ -1272,6 +1337,21 @@ cudaError_t ksg_prepare_attributes()
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(reinterpret_cast<const void *>(&stats_kernel),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+cudaError_t launch_value_sort(const ValueSortJob *jobs, int n_jobs, cudaStream_t st)
+{
+    if (n_jobs <= 0) return cudaSuccess;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(&value_sort_kernel),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kMaxOrderN * 4);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    value_sort_kernel<<<n_jobs, 1024, kMaxOrderN * 4, st>>>(jobs);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_compose(const ComposeJob *jobs, int n_jobs, int max_n, cudaStream_t st)

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <set>
 #include <new>
 #include <string>
 #include <tuple>
@@ -358,6 +359,34 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
     }
     int32_t *cbase = (int32_t *)ctx->ws_cperm.p;
 
+    // Sorted groups with an empty Z, one Y and one X variable and no Theiler
+    // window count by 1-D range searches: sorted copies of their X columns and
+    // of the Y column (one per distinct column of a data set).
+    std::map<std::pair<const te_data *, int>, size_t> vsorted_of;
+    size_t vs_elems = 0;
+    auto col_off = [](const HostGroup *g, te_var v) {
+        return v.proc * g->data->T + g->max_lag - v.lag;
+    };
+    auto want_sorted = [&](const HostGroup *g, int off) {
+        auto key = std::make_pair(g->data, off);
+        if (!vsorted_of.count(key)) {
+            vsorted_of[key] = vs_elems;
+            vs_elems += ((size_t)(g->data->T - g->max_lag) + 3) & ~(size_t)3;
+        }
+    };
+    std::vector<const HostGroup *> fast_groups;
+    for (const HostGroup *g : to_order) {
+        if (!g->z.empty() || g->y.size() != 1 || g->dx != 1 || g->theiler != 0) continue;
+        fast_groups.push_back(g);
+        want_sorted(g, col_off(g, g->y[0]));
+        for (te_var v : g->xvars) want_sorted(g, col_off(g, v));
+    }
+    if (vs_elems) {
+        if ((st = ensure_dev(ctx, ctx->ws_vsort, vs_elems * 4))) return st;
+    }
+    float *vbase = (float *)ctx->ws_vsort.p;
+    std::set<const HostGroup *> fast_set(fast_groups.begin(), fast_groups.end());
+
     // host tables for every class, staged in one pinned block
     struct Plan {
         KsgVariant v;
@@ -461,6 +490,10 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
                 MemberDesc md;
                 md.perm = hm.perm;
                 if (grp_sorted && hm.perm) md.perm = cbase + cperm_of[std::make_pair(g, hm.perm)];
+                md.xsorted = nullptr;
+                if (fast_set.count(g))
+                    md.xsorted = vbase + vsorted_of[std::make_pair(
+                                             g->data, col_off(g, g->xvars[hm.xcol_first]))];
                 md.xcol = xbase + hm.xcol_first;
                 md.out = hm.out;
                 mdesc.push_back(md);
@@ -473,6 +506,8 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
                 gd.n_chunks8 = oit->second.nch;
                 gd.tbox = (const float2 *)(obase + oit->second.tbox);
                 gd.n_tiles256 = oit->second.ntl;
+                if (fast_set.count(g))
+                    gd.ysorted = vbase + vsorted_of[std::make_pair(g->data, col_off(g, g->y[0]))];
             }
             gd.n_qtiles = (N + qsz - 1) / qsz;
             gd.n_mblocks = (gd.n_members + v.m - 1) / v.m;
@@ -520,13 +555,25 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
         max_cn = std::max(max_cn, J.N);
         cjobs.push_back(J);
     }
+    std::vector<ValueSortJob> vjobs;
+    for (auto &kv : vsorted_of) {
+        ValueSortJob J;
+        J.src = kv.first.first->d_series + kv.first.second;
+        J.dst = vbase + kv.second;
+        int n = 0;
+        for (const HostGroup *g : fast_groups)
+            if (g->data == kv.first.first) n = g->data->T - g->max_lag;
+        J.N = n;
+        vjobs.push_back(J);
+    }
     const size_t gbytes = gdesc.size() * sizeof(GroupDesc);
     const size_t mbytes = mdesc.size() * sizeof(MemberDesc);
     const size_t cbytes = cols.size() * sizeof(int);
     const size_t obytes = ojobs.size() * sizeof(OrderJob);
     const size_t jbytes = cjobs.size() * sizeof(ComposeJob);
-    if ((st = ensure_pin(ctx, gbytes + mbytes + cbytes + obytes + jbytes + 64))) return st;
-    if ((st = ensure_dev(ctx, ctx->ws_ojobs, obytes + jbytes + 16))) return st;
+    const size_t vbytes = vjobs.size() * sizeof(ValueSortJob);
+    if ((st = ensure_pin(ctx, gbytes + mbytes + cbytes + obytes + jbytes + vbytes + 64))) return st;
+    if ((st = ensure_dev(ctx, ctx->ws_ojobs, obytes + jbytes + vbytes + 16))) return st;
     if ((st = ensure_dev(ctx, ctx->ws_groups, gbytes + 16))) return st;
     if ((st = ensure_dev(ctx, ctx->ws_members, mbytes + 16))) return st;
     if ((st = ensure_dev(ctx, ctx->ws_cols, cbytes + 16))) return st;
@@ -537,11 +584,12 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
     CK(copy_h2d(ctx, ctx->ws_groups.p, pin, gbytes), "cudaMemcpyAsync");
     CK(copy_h2d(ctx, ctx->ws_members.p, pin + gbytes, mbytes), "cudaMemcpyAsync");
     if (cbytes) CK(copy_h2d(ctx, ctx->ws_cols.p, pin + gbytes + mbytes, cbytes), "cudaMemcpyAsync");
-    if (obytes + jbytes) {
-        std::memcpy(pin + gbytes + mbytes + cbytes, ojobs.data(), obytes);
-        std::memcpy(pin + gbytes + mbytes + cbytes + obytes, cjobs.data(), jbytes);
-        CK(copy_h2d(ctx, ctx->ws_ojobs.p, pin + gbytes + mbytes + cbytes, obytes + jbytes),
-           "cudaMemcpyAsync");
+    if (obytes + jbytes + vbytes) {
+        char *jp = pin + gbytes + mbytes + cbytes;
+        std::memcpy(jp, ojobs.data(), obytes);
+        std::memcpy(jp + obytes, cjobs.data(), jbytes);
+        std::memcpy(jp + obytes + jbytes, vjobs.data(), vbytes);
+        CK(copy_h2d(ctx, ctx->ws_ojobs.p, jp, obytes + jbytes + vbytes), "cudaMemcpyAsync");
     }
 
     if (!ctx->prepared) {
@@ -557,6 +605,12 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
         CK(launch_compose((const ComposeJob *)((char *)ctx->ws_ojobs.p + obytes),
                           (int)cjobs.size(), max_cn, ctx->stream),
            "compose launch");
+        ctx->stats.launches++;
+    }
+    if (!vjobs.empty()) {
+        CK(launch_value_sort((const ValueSortJob *)((char *)ctx->ws_ojobs.p + obytes + jbytes),
+                             (int)vjobs.size(), ctx->stream),
+           "value sort launch");
         ctx->stats.launches++;
     }
     CK(cudaMemsetAsync(ctx->work_dev, 0, 2 * sizeof(unsigned long long), ctx->stream),
@@ -655,7 +709,8 @@ void te_ctx_destroy(te_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     DevBuf *bufs[] = {&ctx->ws_groups, &ctx->ws_members, &ctx->ws_cols,  &ctx->ws_acc,
                       &ctx->ws_keys,   &ctx->ws_perm,    &ctx->ws_stat,  &ctx->ws_dbg,
-                      &ctx->ws_order,  &ctx->ws_ojobs,  &ctx->ws_cperm, &ctx->ws_gauss};
+                      &ctx->ws_order,  &ctx->ws_ojobs,  &ctx->ws_cperm, &ctx->ws_gauss,
+                      &ctx->ws_vsort};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->q_dev) cudaFree(ctx->q_dev);

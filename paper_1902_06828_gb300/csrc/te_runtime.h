@@ -61,7 +61,7 @@ struct te_ctx {
     int q_dev_len = 0;
     // grow-only device workspaces
     teksg::DevBuf ws_groups, ws_members, ws_cols, ws_acc, ws_keys, ws_perm, ws_stat, ws_dbg;
-    teksg::DevBuf ws_order, ws_ojobs, ws_cperm, ws_gauss;
+    teksg::DevBuf ws_order, ws_ojobs, ws_cperm, ws_gauss, ws_vsort;
     // pinned host staging
     void *pin = nullptr;
     size_t pin_cap = 0;

@@ -171,6 +171,7 @@ extern "C" te_status cmi_ksg_static(const float *series_dev, int32_t n_proc, int
         hm[s].perm = s == 0 ? nullptr : perms + (size_t)(s - 1) * N;
         hm[s].xcol = 0;
         hm[s].out = s;
+        hm[s].xsorted = nullptr;
     }
     int *hc = (int *)(hm + S + 1);
     int c = 0;
