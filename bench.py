@@ -445,7 +445,7 @@ def main():
         "gpu_launches": s1["launches"] - s0["launches"],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
-                     "kernel": "ksg_fused_kernel", "kernel_ms_per_launch":
+                     "kernel": "ksg_lane_kernel", "kernel_ms_per_launch":
                      kernel_ms / max(ksg_launches, 1), "launches": ksg_launches,
                      "peak_note": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived)",
                      "work": "3 ops per executed kNN-pass member-pair, 7 per count-pass one",

@@ -97,7 +97,8 @@ struct KsgLaunch {
 // Kernel variants: members per thread and k.  kgen = 0 means k is a template
 // constant; otherwise a runtime k <= TE_MAX_K.
 struct KsgVariant {
-    int m;      // members per thread; 32 selects the member-lane kernel
+    int m;      // members per thread; 32 (64) selects the member-lane kernel with one (two)
+                // members per lane
     int kt;     // template k (0 = runtime k)
     int qt;     // threads per CTA
 };
@@ -105,10 +106,10 @@ struct KsgVariant {
 // member-lane kernel (single-variable X): 32 members x 32 query points per CTA
 constexpr int kLaneQueries = 32;
 constexpr int kLaneThreads = 256;
-inline size_t ksg_lane_smem_bytes(int dyz, int jt)
+inline size_t ksg_lane_smem_bytes(int dyz, int jt, int members = 32)
 {
     const int warps = kLaneThreads / 32;
-    return 4 * ((size_t)dyz * jt + 32 * (size_t)(jt + 4)) +
+    return 4 * ((size_t)dyz * jt + (size_t)members * (jt + 4)) +
            (size_t)warps * (2 * 4 * 8 * 4 + 4 * 4 * (size_t)dyz + 4 * (size_t)(jt / 64));
 }
 

@@ -573,10 +573,12 @@ constexpr int LQ = 4;            // query points per warp
 constexpr int LW = 8;            // warps per CTA
 constexpr int LQC = LQ * LW;     // query points per CTA
 
-template <int KT>
-__global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const KsgLaunch L)
+template <int KT, int MS>
+__global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
+    ksg_lane_kernel(const KsgLaunch L)
 {
     constexpr int KB = KT > 0 ? KT : KMAX;
+    constexpr int MB = 32 * MS;   // members per CTA: MS per lane
     extern __shared__ __align__(16) float smem[];
 
     const long long item = blockIdx.x;
@@ -599,31 +601,38 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float *t_yz = smem;                                   // [dyz][jt]
-    float *t_x = t_yz + dyz * jt;                         // [32][jtp]
-    float *s_dz = t_x + 32 * jtp;                         // [LW][LQ][8]
+    float *t_x = t_yz + dyz * jt;                         // [MB][jtp]
+    float *s_dz = t_x + MB * jtp;                         // [LW][LQ][8]
     float *s_dyz = s_dz + LW * LQ * 8;                    // [LW][LQ][8]
     float *s_q = s_dyz + LW * LQ * 8;                     // [LW][LQ][dyz]
     unsigned *s_bits = reinterpret_cast<unsigned *>(s_q + LW * LQ * dyz);  // [LW][wpt]
-    __shared__ const int32_t *s_mperm[32];
-    __shared__ int s_mxoff[32];
+    __shared__ const int32_t *s_mperm[MB];
+    __shared__ int s_mxoff[MB];
     __shared__ int s_shared_perm;
     __shared__ int s_live[2][LW];
     __shared__ float s_bound[LW][LQ];
-    __shared__ long long s_red[LW][32];
+    __shared__ long long s_red[LW][MB];
     __shared__ float2 s_cqbox[32];
 
-    // ---- this lane's member ----
-    const int mi = mb * 32 + lane;
-    const bool mvalid = mi < G.n_members;
-    const MemberDesc md = L.members[G.member_begin + min(mi, G.n_members - 1)];
-    const int32_t *perm = md.perm;
-    const int xoff = L.cols[md.xcol];
+    // ---- this lane's members: mb * MB + lane + 32 q ----
+    bool mvalid[MS];
+    MemberDesc md[MS];
+#pragma unroll
+    for (int q = 0; q < MS; ++q) {
+        const int mi = mb * MB + lane + 32 * q;
+        mvalid[q] = mi < G.n_members;
+        md[q] = L.members[G.member_begin + min(mi, G.n_members - 1)];
+    }
     if (warp == 0) {
-        s_mperm[lane] = perm;
-        s_mxoff[lane] = xoff;
         const unsigned long long p0 =
-            __shfl_sync(0xffffffffu, (unsigned long long)(uintptr_t)perm, 0);
-        const int same = __all_sync(0xffffffffu, (unsigned long long)(uintptr_t)perm == p0);
+            __shfl_sync(0xffffffffu, (unsigned long long)(uintptr_t)md[0].perm, 0);
+        int same = 1;
+#pragma unroll
+        for (int q = 0; q < MS; ++q) {
+            s_mperm[lane + 32 * q] = md[q].perm;
+            s_mxoff[lane + 32 * q] = L.cols[md[q].xcol];
+            same &= __all_sync(0xffffffffu, (unsigned long long)(uintptr_t)md[q].perm == p0);
+        }
         if (lane == 0) s_shared_perm = same;
     }
 
@@ -633,11 +642,15 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
     const int qbase = qtile * LQC + warp * LQ;   // first query position of this warp
 
     // ---- the warp's query points ----
-    float xi[LQ];
+    float xi[LQ][MS];
 #pragma unroll
     for (int a = 0; a < LQ; ++a) {
         const int qc = min(qbase + a, N - 1);
-        xi[a] = base[xoff + (perm ? perm[qc] : (sorted ? G.sigma[qc] : qc))];
+#pragma unroll
+        for (int q = 0; q < MS; ++q) {
+            const int32_t *pm = md[q].perm;
+            xi[a][q] = base[L.cols[md[q].xcol] + (pm ? pm[qc] : (sorted ? G.sigma[qc] : qc))];
+        }
     }
     for (int e = lane; e < LQ * dyz; e += 32) {
         const int a = e / dyz, d = e - a * dyz;
@@ -692,12 +705,10 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
     // stage the live chunks: thread = (member m, point u) for X, (dim, point)
     // for Y and Z; four chunks per round keep several gathers in flight
     auto stage = [&](int j0, unsigned mask) {
-        const int m = tid >> 3, u = tid & 7;
-        const int32_t *pm = shared_perm ? perm0 : s_mperm[m];
-        const int xo = s_mxoff[m];
+        const int m0 = tid >> 3, u = tid & 7;
         unsigned rest = mask;
         while (rest) {
-            float xv4[4], yz4[4];
+            float xv4[4][MS], yz4[4];
             int cc[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -706,13 +717,19 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
                     cc[q] = __ffs(rest) - 1;
                     rest &= rest - 1;
                 }
-                xv4[q] = 0.f;
                 yz4[q] = 0.f;
+#pragma unroll
+                for (int r = 0; r < MS; ++r) xv4[q][r] = 0.f;
                 if (cc[q] >= 0) {
                     const int j = j0 + cc[q] * 8 + u;
                     if (j < N) {
-                        const int t = pm ? pm[j] : (sorted ? G.sigma[j] : j);
-                        xv4[q] = base[xo + t];
+                        const int tj = sorted ? G.sigma[j] : j;
+#pragma unroll
+                        for (int r = 0; r < MS; ++r) {
+                            const int m = m0 + 32 * r;
+                            const int32_t *pm = shared_perm ? perm0 : s_mperm[m];
+                            xv4[q][r] = base[s_mxoff[m] + (pm ? pm[j] : tj)];
+                        }
                         if (tid < dyz * 8) {
                             const int d = tid >> 3;
                             yz4[q] = sorted ? G.yz[(size_t)d * N + j] : base[yz_off(d) + j];
@@ -723,7 +740,8 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 if (cc[q] < 0) continue;
-                t_x[m * jtp + cc[q] * 8 + u] = xv4[q];
+#pragma unroll
+                for (int r = 0; r < MS; ++r) t_x[(m0 + 32 * r) * jtp + cc[q] * 8 + u] = xv4[q][r];
                 if (tid < dyz * 8) t_yz[(tid >> 3) * jt + cc[q] * 8 + u] = yz4[q];
             }
         }
@@ -794,14 +812,16 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
     int nchk = 0;
 
     // ---------------- pass 1: k nearest joint distances ----------------
-    float buf[LQ][KB];
-    float thr[LQ];
+    float buf[LQ][MS][KB];
+    float thr[LQ][MS];
 #pragma unroll
-    for (int a = 0; a < LQ; ++a) {
+    for (int a = 0; a < LQ; ++a)
 #pragma unroll
-        for (int b = 0; b < KB; ++b) buf[a][b] = CUDART_INF_F;
-        thr[a] = CUDART_INF_F;
-    }
+        for (int q = 0; q < MS; ++q) {
+#pragma unroll
+            for (int b = 0; b < KB; ++b) buf[a][q][b] = CUDART_INF_F;
+            thr[a][q] = CUDART_INF_F;
+        }
     float cbound = CUDART_INF_F;   // snapshot of the CTA's largest bound
     {
         const int home = sorted ? min((qtile * LQC) / jt, ntiles - 1) : 0;
@@ -837,26 +857,32 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
                 const unsigned live4 = (s_bits[warp * wpt + (c >> 6)] >> (4 * ((c >> 3) & 7))) & 0xFu;
                 if (!live4) continue;
                 chunk_dist(j0, c, live4);
-                float xv[JC];
-                load8(t_x + lane * jtp + c, xv);
+                float xv[MS][JC];
+#pragma unroll
+                for (int q = 0; q < MS; ++q) load8(t_x + (lane + 32 * q) * jtp + c, xv[q]);
 #pragma unroll
                 for (int a = 0; a < LQ; ++a) {
                     if (!((live4 >> a) & 1u)) continue;
                     ++executed1;
                     float dv[JC];
                     load8(s_dyz + (warp * LQ + a) * 8, dv);
-                    float D[JC];
 #pragma unroll
-                    for (int u = 0; u < JC; ++u) D[u] = fmaxf(fabsf(__fsub_rn(xi[a], xv[u])), dv[u]);
-                    // one test for the 8 points; the insertions are the rare path
-                    const float mn = fminf(fminf(fminf(D[0], D[1]), fminf(D[2], D[3])),
-                                           fminf(fminf(D[4], D[5]), fminf(D[6], D[7])));
-                    if (mn < thr[a]) {
+                    for (int q = 0; q < MS; ++q) {
+                        float D[JC];
 #pragma unroll
-                        for (int u = 0; u < JC; ++u) {
-                            if (D[u] < thr[a]) {
-                                topk_insert<KB>(buf[a], D[u]);
-                                thr[a] = KT > 0 ? buf[a][KB - 1] : topk_at<KB>(buf[a], k - 1);
+                        for (int u = 0; u < JC; ++u)
+                            D[u] = fmaxf(fabsf(__fsub_rn(xi[a][q], xv[q][u])), dv[u]);
+                        // one test for the 8 points; the insertions are the rare path
+                        const float mn = fminf(fminf(fminf(D[0], D[1]), fminf(D[2], D[3])),
+                                               fminf(fminf(D[4], D[5]), fminf(D[6], D[7])));
+                        if (mn < thr[a][q]) {
+#pragma unroll
+                            for (int u = 0; u < JC; ++u) {
+                                if (D[u] < thr[a][q]) {
+                                    topk_insert<KB>(buf[a][q], D[u]);
+                                    thr[a][q] = KT > 0 ? buf[a][q][KB - 1]
+                                                       : topk_at<KB>(buf[a][q], k - 1);
+                                }
                             }
                         }
                     }
@@ -866,7 +892,10 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
             if (sorted) {
 #pragma unroll
                 for (int a = 0; a < LQ; ++a) {
-                    const float tm = warp_max(thr[a]);
+                    float tl = thr[a][0];
+#pragma unroll
+                    for (int q = 1; q < MS; ++q) tl = fmaxf(tl, thr[a][q]);
+                    const float tm = warp_max(tl);
                     if (lane == 0) s_bound[warp][a] = tm;
                 }
                 __syncwarp();
@@ -880,16 +909,21 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
     __syncthreads();
 
     // ---------------- pass 2: strict range counts ----------------
-    float eps[LQ], cz[LQ], cxz[LQ], cyz[LQ];
+    float eps[LQ][MS], cz[LQ][MS], cxz[LQ][MS], cyz[LQ][MS];
 #pragma unroll
-    for (int a = 0; a < LQ; ++a) {
-        eps[a] = thr[a];
-        cz[a] = cxz[a] = cyz[a] = 0.f;
-    }
+    for (int a = 0; a < LQ; ++a)
+#pragma unroll
+        for (int q = 0; q < MS; ++q) {
+            eps[a][q] = thr[a][q];
+            cz[a][q] = cxz[a][q] = cyz[a][q] = 0.f;
+        }
     const bool prune2 = sorted && dz > 0;   // with empty Z every j counts in n_xz
 #pragma unroll
     for (int a = 0; a < LQ; ++a) {
-        const float em = warp_max(eps[a]);
+        float el = eps[a][0];
+#pragma unroll
+        for (int q = 1; q < MS; ++q) el = fmaxf(el, eps[a][q]);
+        const float em = warp_max(el);
         if (lane == 0) s_bound[warp][a] = prune2 ? em : CUDART_INF_F;
     }
     __syncthreads();   // every warp's pass-2 bounds before the snapshot
@@ -901,13 +935,16 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
     // counts iff eps > 0).  Exactly the counts of the pairwise loop below.
     if (G.ysorted) {
 #pragma unroll
-        for (int a = 0; a < LQ; ++a) {
-            const float e = eps[a];
-            const int self = e > 0.f ? 1 : 0;
-            cz[a] = (float)(N - 1);
-            cxz[a] = (float)(range_count(md.xsorted, N, xi[a], e) - self);
-            cyz[a] = (float)(range_count(G.ysorted, N, s_q[(warp * LQ + a) * dyz], e) - self);
-        }
+        for (int a = 0; a < LQ; ++a)
+#pragma unroll
+            for (int q = 0; q < MS; ++q) {
+                const float e = eps[a][q];
+                const int self = e > 0.f ? 1 : 0;
+                cz[a][q] = (float)(N - 1);
+                cxz[a][q] = (float)(range_count(md[q].xsorted, N, xi[a][q], e) - self);
+                cyz[a][q] =
+                    (float)(range_count(G.ysorted, N, s_q[(warp * LQ + a) * dyz], e) - self);
+            }
     }
     for (int t = 0; t < (G.ysorted ? 0 : ntiles); ++t) {
         const int j0 = t * jt;
@@ -944,8 +981,9 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
             const unsigned live4 = (s_bits[warp * wpt + (c >> 6)] >> (4 * ((c >> 3) & 7))) & 0xFu;
             if (!live4) continue;
             chunk_dist(j0, c, live4);
-            float xv[JC];
-            load8(t_x + lane * jtp + c, xv);
+            float xv[MS][JC];
+#pragma unroll
+            for (int q = 0; q < MS; ++q) load8(t_x + (lane + 32 * q) * jtp + c, xv[q]);
 #pragma unroll
             for (int a = 0; a < LQ; ++a) {
                 if (!((live4 >> a) & 1u)) continue;
@@ -954,9 +992,11 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
                 load8(s_dz + (warp * LQ + a) * 8, zv);
                 load8(s_dyz + (warp * LQ + a) * 8, yv);
 #pragma unroll
-                for (int u = 0; u < JC; ++u)
-                    count3(cz[a], cxz[a], cyz[a], zv[u], yv[u], fabsf(__fsub_rn(xi[a], xv[u])),
-                           eps[a]);
+                for (int q = 0; q < MS; ++q)
+#pragma unroll
+                    for (int u = 0; u < JC; ++u)
+                        count3(cz[a][q], cxz[a][q], cyz[a][q], zv[u], yv[u],
+                               fabsf(__fsub_rn(xi[a][q], xv[q][u])), eps[a][q]);
             }
             __syncwarp();
         }
@@ -964,39 +1004,47 @@ __global__ void __launch_bounds__(LW * 32, KT > 0 ? 3 : 2) ksg_lane_kernel(const
 
     // ---------------- work counters, digamma key ----------------
     if (L.work) {
-        const unsigned mv = __popc(__ballot_sync(0xffffffffu, mvalid));
+        unsigned mv = 0;
+#pragma unroll
+        for (int q = 0; q < MS; ++q) mv += __popc(__ballot_sync(0xffffffffu, mvalid[q]));
         if (lane == 0) {
             const unsigned long long per = (unsigned long long)JC * mv;
             atomicAdd(&L.work[0], (unsigned long long)(executed1 + executed2) * per);
             atomicAdd(&L.work[1], (3ull * executed1 + 7ull * executed2) * per);
         }
     }
-    long long term = 0;
 #pragma unroll
-    for (int a = 0; a < LQ; ++a) {
-        const int nz = (int)cz[a], nxz = (int)cxz[a], nyz = (int)cyz[a];
-        if (qbase + a < N) {
-            term += L.q[nz + 1] - L.q[nxz + 1] - L.q[nyz + 1];
-            if (L.dbg_eps && mvalid && md.out == L.dbg_out) {
-                const int tq = sorted ? G.sigma[qbase + a] : qbase + a;
-                L.dbg_eps[tq] = eps[a];
-                L.dbg_nxz[tq] = nxz;
-                L.dbg_nyz[tq] = nyz;
-                L.dbg_nz[tq] = nz;
+    for (int q = 0; q < MS; ++q) {
+        long long term = 0;
+#pragma unroll
+        for (int a = 0; a < LQ; ++a) {
+            const int nz = (int)cz[a][q], nxz = (int)cxz[a][q], nyz = (int)cyz[a][q];
+            if (qbase + a < N) {
+                term += L.q[nz + 1] - L.q[nxz + 1] - L.q[nyz + 1];
+                if (L.dbg_eps && mvalid[q] && md[q].out == L.dbg_out) {
+                    const int tq = sorted ? G.sigma[qbase + a] : qbase + a;
+                    L.dbg_eps[tq] = eps[a][q];
+                    L.dbg_nxz[tq] = nxz;
+                    L.dbg_nyz[tq] = nyz;
+                    L.dbg_nz[tq] = nz;
+                }
             }
         }
+        s_red[warp][lane + 32 * q] = term;
     }
-    s_red[warp][lane] = term;
     __syncthreads();
     if (warp == 0) {
-        long long sum = 0;
 #pragma unroll
-        for (int b = 0; b < LW; ++b) sum += s_red[b][lane];   // |sum| < 32 * 2^57
-        if (mvalid) {
-            const unsigned long long lo = (unsigned long long)sum & 0xffffffffull;
-            const long long hi = sum >> 32;
-            atomicAdd(&L.acc[2 * md.out], lo);
-            atomicAdd(&L.acc[2 * md.out + 1], (unsigned long long)hi);
+        for (int q = 0; q < MS; ++q) {
+            long long sum = 0;
+#pragma unroll
+            for (int b = 0; b < LW; ++b) sum += s_red[b][lane + 32 * q];   // |sum| < 32 * 2^57
+            if (mvalid[q]) {
+                const unsigned long long lo = (unsigned long long)sum & 0xffffffffull;
+                const long long hi = sum >> 32;
+                atomicAdd(&L.acc[2 * md[q].out], lo);
+                atomicAdd(&L.acc[2 * md[q].out + 1], (unsigned long long)hi);
+            }
         }
     }
 }
@@ -1294,8 +1342,12 @@ const void *kptr()
 const void *select_kernel(const KsgVariant &v, bool dx1)
 {
     if (dx1 && v.m == 32) {
-        if (v.kt == 4) return reinterpret_cast<const void *>(&ksg_lane_kernel<4>);
-        if (v.kt == 0) return reinterpret_cast<const void *>(&ksg_lane_kernel<0>);
+        if (v.kt == 4) return reinterpret_cast<const void *>(&ksg_lane_kernel<4, 1>);
+        if (v.kt == 0) return reinterpret_cast<const void *>(&ksg_lane_kernel<0, 1>);
+        return nullptr;
+    }
+    if (dx1 && v.m == 64) {
+        if (v.kt == 4) return reinterpret_cast<const void *>(&ksg_lane_kernel<4, 2>);
         return nullptr;
     }
     if (dx1) {
@@ -1322,7 +1374,8 @@ const void *select_kernel(const KsgVariant &v, bool dx1)
 cudaError_t ksg_prepare_attributes()
 {
     const KsgVariant vs[] = {{4, 4, QT},  {8, 4, QT},  {16, 4, QT}, {2, 0, QT},
-                             {2, 4, QT},  {32, 4, LW * 32}, {32, 0, LW * 32}};
+                             {2, 4, QT},  {32, 4, LW * 32}, {32, 0, LW * 32},
+                             {64, 4, LW * 32}};
     for (const auto &v : vs)
         for (int d = 0; d < 2; ++d) {
             const void *f = select_kernel(v, d == 0);

@@ -409,12 +409,16 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
         KsgVariant v{4, 4, 128};
         if (dx1) {
             v = KsgVariant{32, k4 ? 4 : 0, kLaneThreads};   // member-lane kernel
+            // two members per lane when every group has enough members to fill them
+            size_t min_members = SIZE_MAX;
+            for (const HostGroup *g : gs) min_members = std::min(min_members, g->members.size());
+            if (k4 && min_members >= 64) v.m = 64;
         } else if (!k4) {
             v = KsgVariant{2, 0, 128};
         } else {
             v.m = 4;
         }
-        const bool lanek = v.m == 32;
+        const bool lanek = v.m == 32 || v.m == 64;
         const int qsz = lanek ? kLaneQueries : 128;
         int rows_t = 0, rows_q = 0, maxN = 0;
         for (const HostGroup *g : gs) {
@@ -446,7 +450,7 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
                 maxdyz = std::max(maxdyz, (int)(g->y.size() + g->z.size()));
             jt = 256;
             if (maxN < jt) jt = std::max(64, (maxN + 63) & ~63);
-            smem = ksg_lane_smem_bytes(maxdyz, jt);
+            smem = ksg_lane_smem_bytes(maxdyz, jt, v.m);
         } else {
             jt = jt_for(40 * 1024);
             if (jt < 64) jt = jt_for(190 * 1024);

@@ -121,6 +121,39 @@ def test_shapes_and_variants(te, ctx, T, n_proc, x, y, z, k, w):
         np.testing.assert_array_equal(g[c], o[c])
 
 
+CASES_WIDE = [
+    # (T, z, theiler)  71 members: two members per lane, second member block ragged
+    (301, [], 0),                                   # empty Z (sorted-column counts)
+    (389, [(1, 1), (2, 2)], 0),
+    (257, [(1, 1)], 3),
+]
+
+
+@pytest.mark.parametrize("T,z,w", CASES_WIDE)
+def test_two_members_per_lane(te, ctx, T, z, w):
+    """Groups of at least 64 members run two members per lane; keys stay
+    bit-exact, including the ragged last member block."""
+    rng = np.random.default_rng(T + 17)
+    s = rng.normal(size=(3, T))
+    s[1, 1:] += 0.5 * s[0, :-1]
+    s = synth.standardise_jitter(s, T)
+    data = te.te_data_create(ctx, s)
+    x, y, S = [(0, 1)], [(1, 0)], 70
+    ml = max(l for _, l in x + y + z)
+    cmi, keys = te.cmi_ksg(ctx, data, x, y, z, k=4, theiler=w, max_lag=ml, n_surr=S, seed=8,
+                           stream_tag=T, return_keys=True)
+    ok, ik, ip, perms = _oracle_members(s, x, y, z, 4, w, ml, S, 8, T)
+    assert keys == ok
+    assert np.array_equal(cmi, ik) and _close(cmi, ip)
+    for member in (33, 70):      # second slot of a lane; last (ragged) block
+        g = te.cmi_ksg_debug(ctx, data, x, y, z, member=member, k=4, theiler=w, max_lag=ml,
+                             n_surr=S, seed=8, stream_tag=T)
+        o = oksg.cmi_ksg(s, x, y, z, k=4, theiler=w, max_lag=ml, perm=perms[member - 1],
+                         per_point=True)
+        for c in ("eps", "n_xz", "n_yz", "n_z"):
+            np.testing.assert_array_equal(g[c], o[c])
+
+
 def test_duplicates_and_minimum_size(te, ctx):
     s = np.array([[0, 0, 0, 5, 1, 1], [0, 0, 0, 5, 2, 2]], np.float32)
     data = te.te_data_create(ctx, s)
