@@ -780,10 +780,15 @@ __global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
     };
 
     // d_Z and d_YZ of the live queries against the 8 points of the chunk at c;
-    // lane = (query a, point u); masked pairs (past N, self, Theiler band) = +inf
-    auto chunk_dist = [&](int j0, int c, unsigned live4) {
+    // lane = (query a, point u); masked pairs (past N, self, Theiler band) = +inf.
+    // Returns live4 without the queries whose 8 points all lie at or beyond the
+    // query's bound in the pass's shared subspace (d_YZ in pass 1, d_Z in pass
+    // 2): with the bound >= every member's threshold or eps, no member can insert
+    // or count one of them.
+    auto chunk_dist = [&](int j0, int c, unsigned live4, bool pass1) {
         const int a = lane >> 3, u = lane & 7;
         float dzv = -CUDART_INF_F, dyzv = -CUDART_INF_F;
+        bool keep = false;
         if ((live4 >> a) & 1u) {
             const float *qc = s_q + (warp * LQ + a) * dyz;
             for (int d = dy; d < dyz; ++d)
@@ -798,10 +803,18 @@ __global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
                 dzv = CUDART_INF_F;
                 dyzv = CUDART_INF_F;
             }
+            keep = (pass1 ? dyzv : dzv) < s_bound[warp][a];
         }
+        // the ballot also orders these stores after every lane's reads of the
+        // previous chunk's distances
+        const unsigned kb = __ballot_sync(0xffffffffu, keep);
         s_dz[(warp * LQ + a) * 8 + u] = dzv;
         s_dyz[(warp * LQ + a) * 8 + u] = dyzv;
+        unsigned out = 0;
+#pragma unroll
+        for (int b = 0; b < LQ; ++b) out |= ((kb >> (8 * b)) & 0xFFu) ? (1u << b) : 0u;
         __syncwarp();
+        return out;
     };
 
     const int ntiles = (N + jt - 1) / jt;
@@ -854,9 +867,10 @@ __global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
             while (rest) {
                 const int c = (__ffs(rest) - 1) * JC;
                 rest &= rest - 1;
-                const unsigned live4 = (s_bits[warp * wpt + (c >> 6)] >> (4 * ((c >> 3) & 7))) & 0xFu;
+                unsigned live4 = (s_bits[warp * wpt + (c >> 6)] >> (4 * ((c >> 3) & 7))) & 0xFu;
                 if (!live4) continue;
-                chunk_dist(j0, c, live4);
+                live4 = chunk_dist(j0, c, live4, true);
+                if (!live4) continue;
                 float xv[MS][JC];
 #pragma unroll
                 for (int q = 0; q < MS; ++q) load8(t_x + (lane + 32 * q) * jtp + c, xv[q]);
@@ -978,9 +992,10 @@ __global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
         while (rest) {
             const int c = (__ffs(rest) - 1) * JC;
             rest &= rest - 1;
-            const unsigned live4 = (s_bits[warp * wpt + (c >> 6)] >> (4 * ((c >> 3) & 7))) & 0xFu;
+            unsigned live4 = (s_bits[warp * wpt + (c >> 6)] >> (4 * ((c >> 3) & 7))) & 0xFu;
             if (!live4) continue;
-            chunk_dist(j0, c, live4);
+            live4 = chunk_dist(j0, c, live4, false);
+            if (!live4) continue;
             float xv[MS][JC];
 #pragma unroll
             for (int q = 0; q < MS; ++q) load8(t_x + (lane + 32 * q) * jtp + c, xv[q]);
@@ -1411,8 +1426,14 @@ cudaError_t launch_compose(const ComposeJob *jobs, int n_jobs, int max_n, cudaSt
 {
     if (n_jobs <= 0) return cudaSuccess;
     const int bx = (max_n + 255) / 256 < 64 ? (max_n + 255) / 256 : 64;
-    compose_kernel<<<dim3(bx, n_jobs), 256, 0, st>>>(jobs);
-    return cudaGetLastError();
+    // one grid row per job; the grid's y extent is at most 65535
+    for (int j0 = 0; j0 < n_jobs; j0 += 65535) {
+        const int ny = n_jobs - j0 < 65535 ? n_jobs - j0 : 65535;
+        compose_kernel<<<dim3(bx, ny), 256, 0, st>>>(jobs + j0);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_order(const OrderJob *jobs, int n_jobs, cudaStream_t st)

@@ -154,6 +154,29 @@ def test_two_members_per_lane(te, ctx, T, z, w):
             np.testing.assert_array_equal(g[c], o[c])
 
 
+def test_batch_beyond_grid_limits(te, ctx):
+    """330 jobs x 200 surrogates: more composed permutations (66,000) than one
+    launch's grid y extent; sampled jobs equal their single calls and the
+    oracle."""
+    T, S = 120, 200
+    rng = np.random.default_rng(5)
+    s = synth.standardise_jitter(rng.normal(size=(6, T)), 5)
+    data = te.te_data_create(ctx, s)
+    y, z = [(0, 0)], [(0, 1), (1, 2)]
+    cands = [(p, l) for p in range(1, 6) for l in range(1, 6) if (p, l) != (1, 2)]
+    jobs = [te.Job(data, [cands[a % len(cands)]], y, z, k=4, max_lag=5, n_surr=S, seed=4,
+                   stream_tag=a) for a in range(330)]
+    cmi, keys = te.cmi_ksg_batch(ctx, jobs, return_keys=True)
+    for a in (0, 167, 329):
+        j = jobs[a]
+        one, okeys = te.cmi_ksg(ctx, data, j.x, y, z, k=4, max_lag=5, n_surr=S, seed=4,
+                                stream_tag=a, return_keys=True)
+        assert keys[a] == okeys
+        assert np.array_equal(cmi[a], one)
+    ok, _, _, _ = _oracle_members(s, jobs[329].x, y, z, 4, 0, 5, S, 4, 329)
+    assert keys[329] == ok
+
+
 def test_duplicates_and_minimum_size(te, ctx):
     s = np.array([[0, 0, 0, 5, 1, 1], [0, 0, 0, 5, 2, 2]], np.float32)
     data = te.te_data_create(ctx, s)
