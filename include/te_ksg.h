@@ -280,7 +280,7 @@ typedef uint64_t te_ticket;
 
 typedef struct {
     size_t hbm_budget_bytes;  /* device bytes admitted jobs may hold at once (0: 4 GiB); a job
-                                 needs about 8 S N + 4 N (1 + dy + dz) + 64 (S + 1) bytes */
+                                 needs about 12 S N + 4 N (2 + dy + dz) + 64 (S + 1) bytes */
     int32_t max_inflight;     /* batches on the device at once, 1..8 (0: 2) */
     int32_t max_batch_jobs;   /* jobs per batch (0: 2048) */
 } te_serve_config;

@@ -2,6 +2,7 @@
 // Not part of the public ABI (include/te_ksg.h is).
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (type only; the encoder is fetched through the runtime)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -91,7 +92,13 @@ struct KsgLaunch {
     int dbg_out;
     int jt;                        // points per staged j tile
     unsigned long long *work;      // [0] += member-pair evaluations executed (both passes),
-                                   // [1] += algorithmic ops of those evaluations
+                                   // [1] += algorithmic ops of those evaluations,
+                                   // [2] != 0: a tile copy did not complete in time
+    // member-lane kernel with tensor-memory-access staging: X value of member
+    // row r (the member's index in this launch) at position j is
+    // xval[r * xpitch + j] (positions in the group's order, zero past N)
+    const float *xval;
+    long long xpitch;
 };
 
 // Kernel variants: members per thread and k.  kgen = 0 means k is a template
@@ -101,6 +108,8 @@ struct KsgVariant {
                 // members per lane
     int kt;     // template k (0 = runtime k)
     int qt;     // threads per CTA
+    bool tma;   // member-lane kernel: X tiles copied by the tensor memory accelerator
+                // from the launch's X-value rows (false: gathered by the threads)
 };
 
 // member-lane kernel (single-variable X): 32 members x 32 query points per CTA
@@ -113,8 +122,24 @@ inline size_t ksg_lane_smem_bytes(int dyz, int jt, int members = 32)
            (size_t)warps * (2 * 4 * 8 * 4 + 4 * 4 * (size_t)dyz + 4 * (size_t)(jt / 64));
 }
 
+// TMA-staged lane kernel: X tiles are [jt / 32 segments][members][32 points],
+// 128-byte swizzled, 1024-byte aligned (hence the slack)
+inline size_t ksg_lane_tma_smem_bytes(int dyz, int jt, int members)
+{
+    const int warps = kLaneThreads / 32;
+    return 1024 + 4 * ((size_t)dyz * jt + (size_t)members * jt) +
+           (size_t)warps * (2 * 4 * 8 * 4 + 4 * 4 * (size_t)dyz + 4 * (size_t)(jt / 64));
+}
+
+// tmap: the 2-D tensor map of L.xval for TMA variants (nullptr otherwise)
 cudaError_t launch_ksg(const KsgLaunch &L, const KsgVariant &v, long long n_items, bool dx1,
-                       size_t smem_bytes, cudaStream_t st);
+                       size_t smem_bytes, cudaStream_t st, const CUtensorMap *tmap = nullptr);
+// X-value rows of every member of the launch (L.xval, row pitch L.xpitch floats)
+cudaError_t launch_xval(const KsgLaunch &L, int n_rows, cudaStream_t st);
+// tensor map over rows x pitch floats at xval, box = 32 points x box_rows rows,
+// 128-byte swizzle; cudaErrorNotSupported when the driver lacks the encoder
+cudaError_t encode_xval_map(CUtensorMap *map, const float *xval, long long pitch, int rows,
+                            int box_rows);
 cudaError_t ksg_prepare_attributes();
 
 // dynamic shared memory of the fused kernel: the staged tile, the query-side

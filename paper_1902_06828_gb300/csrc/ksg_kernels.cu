@@ -17,9 +17,12 @@
 // Estimator: Kraskov's I^(1) extended to CMI (Methods, "Coupled logistic maps
 // process"); surrogates permute X only (Statistical tests, "Maximum statistic
 // test").  Max-norm distances are exact float32 |a - b| (no FMA, no fast-math).
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <math_constants.h>
 #include <stdint.h>
+
+#include <cstring>
 
 #include "ksg_internal.h"
 
@@ -568,14 +571,40 @@ __device__ __forceinline__ int range_count(const float *__restrict__ col, int n,
 // point's current k-th distance (pass 1) or eps (pass 2), so the bounds are
 // as tight as a single point allows.  d_Z and d_YZ of a chunk are computed
 // lane-parallel over (query, point) pairs and read back as broadcasts; the X
-// values of a lane's member come from a padded [member][point] tile.
+// values of a lane's member come from a [member][point] tile in shared memory.
+// With TMA = true that tile is copied by the tensor memory accelerator from the
+// launch's X-value rows (one 2-D box of 32 points x all CTA members per live
+// 32-point segment, 128-byte swizzled); otherwise the threads gather it
+// through the members' permutations.
 constexpr int LQ = 4;            // query points per warp
 constexpr int LW = 8;            // warps per CTA
 constexpr int LQC = LQ * LW;     // query points per CTA
+constexpr unsigned kTileSpinLimit = 1u << 24;   // bounded waits on a tile copy
 
-template <int KT, int MS>
+__device__ __forceinline__ uint32_t lane_smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// bounded wait for the phase of parity `parity` of the mbarrier at `addr`
+__device__ __forceinline__ bool tile_wait(uint32_t addr, uint32_t parity)
+{
+    for (unsigned it = 0; it < kTileSpinLimit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+template <int KT, int MS, bool TMA>
 __global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
-    ksg_lane_kernel(const KsgLaunch L)
+    ksg_lane_kernel(const KsgLaunch L, const __grid_constant__ CUtensorMap tmx)
 {
     constexpr int KB = KT > 0 ? KT : KMAX;
     constexpr int MB = 32 * MS;   // members per CTA: MS per lane
@@ -600,9 +629,18 @@ __global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
     const bool sorted = G.sigma != nullptr;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float *t_yz = smem;                                   // [dyz][jt]
-    float *t_x = t_yz + dyz * jt;                         // [MB][jtp]
-    float *s_dz = t_x + MB * jtp;                         // [LW][LQ][8]
+    float *t_yz, *t_x, *s_dz;
+    if constexpr (TMA) {
+        // [jt / 32][MB][32] X tile on a 1024-byte boundary (the swizzle atom)
+        const uint32_t pad = (1024u - (lane_smem_u32(smem) & 1023u)) & 1023u;
+        t_x = smem + pad / 4;
+        t_yz = t_x + MB * jt;                             // [dyz][jt]
+        s_dz = t_yz + dyz * jt;                           // [LW][LQ][8]
+    } else {
+        t_yz = smem;                                      // [dyz][jt]
+        t_x = t_yz + dyz * jt;                            // [MB][jtp]
+        s_dz = t_x + MB * jtp;                            // [LW][LQ][8]
+    }
     float *s_dyz = s_dz + LW * LQ * 8;                    // [LW][LQ][8]
     float *s_q = s_dyz + LW * LQ * 8;                     // [LW][LQ][dyz]
     unsigned *s_bits = reinterpret_cast<unsigned *>(s_q + LW * LQ * dyz);  // [LW][wpt]
@@ -613,6 +651,18 @@ __global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
     __shared__ float s_bound[LW][LQ];
     __shared__ long long s_red[LW][MB];
     __shared__ float2 s_cqbox[32];
+    __shared__ __align__(8) unsigned long long s_tbar;   // tile-copy mbarrier (TMA)
+    const uint32_t tbar = lane_smem_u32(&s_tbar);
+    uint32_t tphase = 0;
+    if constexpr (TMA) {
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tbar));
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmx))
+                         : "memory");
+        }
+    }
 
     // ---- this lane's members: mb * MB + lane + 32 q ----
     bool mvalid[MS];
@@ -623,7 +673,7 @@ __global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
         mvalid[q] = mi < G.n_members;
         md[q] = L.members[G.member_begin + min(mi, G.n_members - 1)];
     }
-    if (warp == 0) {
+    if (!TMA && warp == 0) {
         const unsigned long long p0 =
             __shfl_sync(0xffffffffu, (unsigned long long)(uintptr_t)md[0].perm, 0);
         int same = 1;
@@ -648,8 +698,13 @@ __global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
         const int qc = min(qbase + a, N - 1);
 #pragma unroll
         for (int q = 0; q < MS; ++q) {
-            const int32_t *pm = md[q].perm;
-            xi[a][q] = base[L.cols[md[q].xcol] + (pm ? pm[qc] : (sorted ? G.sigma[qc] : qc))];
+            if constexpr (TMA) {
+                const int row = G.member_begin + min(mb * MB + lane + 32 * q, G.n_members - 1);
+                xi[a][q] = L.xval[(size_t)row * L.xpitch + qc];
+            } else {
+                const int32_t *pm = md[q].perm;
+                xi[a][q] = base[L.cols[md[q].xcol] + (pm ? pm[qc] : (sorted ? G.sigma[qc] : qc))];
+            }
         }
     }
     for (int e = lane; e < LQ * dyz; e += 32) {
@@ -744,6 +799,69 @@ __global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
                 for (int r = 0; r < MS; ++r) t_x[(m0 + 32 * r) * jtp + cc[q] * 8 + u] = xv4[q][r];
                 if (tid < dyz * 8) t_yz[(tid >> 3) * jt + cc[q] * 8 + u] = yz4[q];
             }
+        }
+    };
+
+    // Stage the tile's live chunks and make them visible to every thread; false
+    // (identical in every thread) when a tile copy did not complete in time, in
+    // which case the error flag is set and the caller returns.
+    auto stage_all = [&](int j0, int jn, unsigned mask) {
+        if constexpr (TMA) {
+            if (tid == 0) {
+                const int nseg = jt >> 5;
+                unsigned segs = 0;
+                for (int sg = 0; sg < nseg; ++sg)
+                    if ((mask >> (4 * sg)) & 0xFu) segs |= 1u << sg;
+                const uint32_t bytes = (uint32_t)__popc(segs) * (uint32_t)(MB * 128);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                             ::"r"(tbar), "r"(bytes) : "memory");
+                const int row0 = G.member_begin + mb * MB;
+                const uint32_t dst0 = lane_smem_u32(t_x);
+                while (segs) {
+                    const int sg = __ffs(segs) - 1;
+                    segs &= segs - 1;
+                    asm volatile(
+                        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx"
+                        "::bytes [%0], [%1, {%2, %3}], [%4];"
+                        ::"r"(dst0 + (uint32_t)(sg * MB * 128)),
+                          "l"(reinterpret_cast<uint64_t>(&tmx)), "r"(j0 + 32 * sg), "r"(row0),
+                          "r"(tbar)
+                        : "memory");
+                }
+            }
+            // Y and Z of the whole tile, coalesced (jt <= blockDim)
+            if (tid < jn)
+                for (int d = 0; d < dyz; ++d)
+                    t_yz[d * jt + tid] =
+                        sorted ? G.yz[(size_t)d * N + j0 + tid] : base[yz_off(d) + j0 + tid];
+            const bool ok = tile_wait(tbar, tphase);
+            tphase ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) {
+                    atomicExch(&L.work[2], 1ull);
+                    tile_wait(tbar, tphase ^ 1u);   // let copies still in flight land
+                }
+                return false;
+            }
+            return true;
+        } else {
+            stage(j0, mask);
+            __syncthreads();
+            return true;
+        }
+    };
+
+    // X values of member slot q (member lane + 32 q) at the 8 points of chunk c
+    auto load_x = [&](int c, int q, float (&v)[JC]) {
+        if constexpr (TMA) {
+            const float *row = t_x + ((c >> 5) * MB + lane + 32 * q) * 32;
+            const int k0 = (c & 31) >> 2, sw = lane & 7;
+            const float4 lo = *reinterpret_cast<const float4 *>(row + ((k0 ^ sw) << 2));
+            const float4 hi = *reinterpret_cast<const float4 *>(row + (((k0 + 1) ^ sw) << 2));
+            v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
+            v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
+        } else {
+            load8(t_x + (lane + 32 * q) * jtp + c, v);
         }
     };
 
@@ -861,8 +979,7 @@ __global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
             for (int b = 0; b < LW; ++b) any |= s_live[buf_i][b];
             if (!any) continue;
             const unsigned mask = cta_mask(jn);
-            stage(j0, mask);
-            __syncthreads();
+            if (!stage_all(j0, jn, mask)) return;
             unsigned rest = mask;
             while (rest) {
                 const int c = (__ffs(rest) - 1) * JC;
@@ -873,7 +990,7 @@ __global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
                 if (!live4) continue;
                 float xv[MS][JC];
 #pragma unroll
-                for (int q = 0; q < MS; ++q) load8(t_x + (lane + 32 * q) * jtp + c, xv[q]);
+                for (int q = 0; q < MS; ++q) load_x(c, q, xv[q]);
 #pragma unroll
                 for (int a = 0; a < LQ; ++a) {
                     if (!((live4 >> a) & 1u)) continue;
@@ -986,8 +1103,7 @@ __global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
         for (int b = 0; b < LW; ++b) any |= s_live[buf_i][b];
         if (!any) continue;
         const unsigned mask = cta_mask(jn);
-        stage(j0, mask);
-        __syncthreads();
+        if (!stage_all(j0, jn, mask)) return;
         unsigned rest = mask;
         while (rest) {
             const int c = (__ffs(rest) - 1) * JC;
@@ -998,7 +1114,7 @@ __global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
             if (!live4) continue;
             float xv[MS][JC];
 #pragma unroll
-            for (int q = 0; q < MS; ++q) load8(t_x + (lane + 32 * q) * jtp + c, xv[q]);
+            for (int q = 0; q < MS; ++q) load_x(c, q, xv[q]);
 #pragma unroll
             for (int a = 0; a < LQ; ++a) {
                 if (!((live4 >> a) & 1u)) continue;
@@ -1357,12 +1473,16 @@ const void *kptr()
 const void *select_kernel(const KsgVariant &v, bool dx1)
 {
     if (dx1 && v.m == 32) {
-        if (v.kt == 4) return reinterpret_cast<const void *>(&ksg_lane_kernel<4, 1>);
-        if (v.kt == 0) return reinterpret_cast<const void *>(&ksg_lane_kernel<0, 1>);
+        if (v.kt == 4)
+            return v.tma ? reinterpret_cast<const void *>(&ksg_lane_kernel<4, 1, true>)
+                         : reinterpret_cast<const void *>(&ksg_lane_kernel<4, 1, false>);
+        if (v.kt == 0)
+            return v.tma ? reinterpret_cast<const void *>(&ksg_lane_kernel<0, 1, true>)
+                         : reinterpret_cast<const void *>(&ksg_lane_kernel<0, 1, false>);
         return nullptr;
     }
     if (dx1 && v.m == 64) {
-        if (v.kt == 4) return reinterpret_cast<const void *>(&ksg_lane_kernel<4, 2>);
+        if (v.kt == 4 && v.tma) return reinterpret_cast<const void *>(&ksg_lane_kernel<4, 2, true>);
         return nullptr;
     }
     if (dx1) {
@@ -1390,7 +1510,8 @@ cudaError_t ksg_prepare_attributes()
 {
     const KsgVariant vs[] = {{4, 4, QT},  {8, 4, QT},  {16, 4, QT}, {2, 0, QT},
                              {2, 4, QT},  {32, 4, LW * 32}, {32, 0, LW * 32},
-                             {64, 4, LW * 32}};
+                             {32, 4, LW * 32, true}, {32, 0, LW * 32, true},
+                             {64, 4, LW * 32, true}};
     for (const auto &v : vs)
         for (int d = 0; d < 2; ++d) {
             const void *f = select_kernel(v, d == 0);
@@ -1444,15 +1565,83 @@ cudaError_t launch_order(const OrderJob *jobs, int n_jobs, cudaStream_t st)
 }
 
 cudaError_t launch_ksg(const KsgLaunch &L, const KsgVariant &v, long long n_items, bool dx1,
-                       size_t smem_bytes, cudaStream_t st)
+                       size_t smem_bytes, cudaStream_t st, const CUtensorMap *tmap)
 {
     const void *f = select_kernel(v, dx1);
     if (!f) return cudaErrorInvalidValue;
     if (n_items <= 0) return cudaSuccess;
     if (n_items > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const bool lane = dx1 && (v.m == 32 || v.m == 64);
+    if (v.tma && (!lane || !tmap || !L.xval || !L.work || L.jt > LW * 32 || (L.jt & 31)))
+        return cudaErrorInvalidValue;
     KsgLaunch arg = L;
-    void *args[] = {&arg};
+    CUtensorMap map;
+    if (tmap) map = *tmap;
+    else std::memset(&map, 0, sizeof map);
+    void *args[] = {&arg, &map};
     return cudaLaunchKernel(f, dim3((unsigned)n_items), dim3(v.qt), args, smem_bytes, st);
+}
+
+// One CTA per member row: the member's X values in its group's point order
+// (through the composed permutation, the group's order, or as is), zero from
+// N to the row pitch.
+__global__ void xval_kernel(const KsgLaunch L, int n_rows)
+{
+    const int r = blockIdx.x;
+    if (r >= n_rows) return;
+    int glo = 0, ghi = L.n_groups - 1;
+    while (glo < ghi) {
+        const int mid = (glo + ghi + 1) >> 1;
+        if (L.groups[mid].member_begin <= r) glo = mid;
+        else ghi = mid - 1;
+    }
+    const GroupDesc &G = L.groups[glo];
+    const MemberDesc md = L.members[r];
+    const float *src = G.base + L.cols[md.xcol];
+    float *dst = const_cast<float *>(L.xval) + (size_t)r * L.xpitch;
+    for (long long j = threadIdx.x; j < L.xpitch; j += blockDim.x) {
+        float v = 0.f;
+        if (j < G.N) {
+            const int jj = (int)j;
+            v = src[md.perm ? md.perm[jj] : (G.sigma ? G.sigma[jj] : jj)];
+        }
+        dst[j] = v;
+    }
+}
+
+cudaError_t launch_xval(const KsgLaunch &L, int n_rows, cudaStream_t st)
+{
+    if (n_rows <= 0) return cudaSuccess;
+    xval_kernel<<<n_rows, 256, 0, st>>>(L, n_rows);
+    return cudaGetLastError();
+}
+
+cudaError_t encode_xval_map(CUtensorMap *map, const float *xval, long long pitch, int rows,
+                            int box_rows)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return cudaErrorNotSupported;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    if (rows < 1 || pitch < 32 || (pitch & 3) || box_rows < 1 || box_rows > 256 ||
+        (reinterpret_cast<uintptr_t>(xval) & 15))
+        return cudaErrorInvalidValue;
+    const cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch * 4};
+    const cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                              const_cast<float *>(xval), dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_perms(int32_t *out, long long stride, int n, uint64_t seed, uint64_t target,

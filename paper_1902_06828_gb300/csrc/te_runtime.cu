@@ -285,6 +285,8 @@ te_status finish_groups(te_ctx *ctx)
     ctx->stats.ksg_ops += ctx->work_host[1];
     ctx->stats.estimates += ctx->pend_members;
     ctx->pend_timed = 0;
+    if (ctx->work_host[2])
+        return fail(ctx, TE_ETIMEOUT, "a KSG tile copy did not complete in time");
     return TE_OK;
 }
 
@@ -396,7 +398,11 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
         long long items;
         size_t g_off, m_off, c_off;  // element offsets into the tables
         int n_groups;
+        int rows = 0;                // TMA lane kernel: member rows, row pitch (floats),
+        long long pitch = 0;         // byte offset of the rows in ws_xval
+        size_t xoff = 0;
     };
+    size_t xval_bytes = 0;
     std::vector<Plan> plans;
     std::vector<GroupDesc> gdesc;
     std::vector<MemberDesc> mdesc;
@@ -408,7 +414,7 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
         auto &gs = kv.second;
         KsgVariant v{4, 4, 128};
         if (dx1) {
-            v = KsgVariant{32, k4 ? 4 : 0, kLaneThreads};   // member-lane kernel
+            v = KsgVariant{32, k4 ? 4 : 0, kLaneThreads, true};   // member-lane kernel, TMA tiles
             // two members per lane when every group has enough members to fill them
             size_t min_members = SIZE_MAX;
             for (const HostGroup *g : gs) min_members = std::min(min_members, g->members.size());
@@ -450,7 +456,7 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
                 maxdyz = std::max(maxdyz, (int)(g->y.size() + g->z.size()));
             jt = 256;
             if (maxN < jt) jt = std::max(64, (maxN + 63) & ~63);
-            smem = ksg_lane_smem_bytes(maxdyz, jt, v.m);
+            smem = ksg_lane_tma_smem_bytes(maxdyz, jt, v.m);
         } else {
             jt = jt_for(40 * 1024);
             if (jt < 64) jt = jt_for(190 * 1024);
@@ -468,6 +474,14 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
         p.m_off = mdesc.size();
         p.c_off = cols.size();
         p.n_groups = (int)gs.size();
+        if (v.tma) {
+            size_t rows = 0;
+            for (const HostGroup *g : gs) rows += g->members.size();
+            p.rows = (int)rows;
+            p.pitch = std::max(32, (maxN + 3) & ~3);
+            p.xoff = xval_bytes;
+            xval_bytes += ((size_t)p.rows * (size_t)p.pitch * 4 + 255) & ~(size_t)255;
+        }
         long long item = 0;
         for (const HostGroup *g : gs) {
             const te_data *d = g->data;
@@ -581,6 +595,7 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
     if ((st = ensure_dev(ctx, ctx->ws_groups, gbytes + 16))) return st;
     if ((st = ensure_dev(ctx, ctx->ws_members, mbytes + 16))) return st;
     if ((st = ensure_dev(ctx, ctx->ws_cols, cbytes + 16))) return st;
+    if (xval_bytes && (st = ensure_dev(ctx, ctx->ws_xval, xval_bytes))) return st;
     char *pin = (char *)ctx->pin;
     std::memcpy(pin, gdesc.data(), gbytes);
     std::memcpy(pin + gbytes, mdesc.data(), mbytes);
@@ -617,7 +632,7 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
            "value sort launch");
         ctx->stats.launches++;
     }
-    CK(cudaMemsetAsync(ctx->work_dev, 0, 2 * sizeof(unsigned long long), ctx->stream),
+    CK(cudaMemsetAsync(ctx->work_dev, 0, 3 * sizeof(unsigned long long), ctx->stream),
        "cudaMemsetAsync");
     CK(cudaEventRecord(ctx->ev_a, ctx->stream), "cudaEventRecord");
     for (const Plan &p : plans) {
@@ -635,12 +650,23 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
         L.dbg_out = dbg_out;
         L.jt = p.jt;
         L.work = ctx->work_dev;
-        CK(launch_ksg(L, p.v, p.items, p.dx1, p.smem, ctx->stream), "KSG kernel launch");
+        if (p.v.tma) {
+            L.xval = (const float *)((char *)ctx->ws_xval.p + p.xoff);
+            L.xpitch = p.pitch;
+            CUtensorMap map;
+            CK(encode_xval_map(&map, L.xval, p.pitch, p.rows, p.v.m), "tensor map encode");
+            CK(launch_xval(L, p.rows, ctx->stream), "X-value launch");
+            ctx->stats.launches++;
+            CK(launch_ksg(L, p.v, p.items, p.dx1, p.smem, ctx->stream, &map),
+               "KSG kernel launch");
+        } else {
+            CK(launch_ksg(L, p.v, p.items, p.dx1, p.smem, ctx->stream), "KSG kernel launch");
+        }
         ctx->stats.launches++;
         ctx->stats.ksg_launches++;
     }
     CK(cudaEventRecord(ctx->ev_b, ctx->stream), "cudaEventRecord");
-    CK(copy_d2h(ctx, ctx->work_host, ctx->work_dev, 2 * sizeof(unsigned long long)),
+    CK(copy_d2h(ctx, ctx->work_host, ctx->work_dev, 3 * sizeof(unsigned long long)),
        "cudaMemcpyAsync");
     CK(launch_finalize((const unsigned long long *)ctx->ws_acc.p, (long long *)ctx->ws_keys.p,
                        n_out, ctx->stream),
@@ -687,8 +713,8 @@ te_status te_ctx_create(int device, te_ctx **out)
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&ctx->ev_a) != cudaSuccess || cudaEventCreate(&ctx->ev_b) != cudaSuccess ||
-        cudaMalloc(&ctx->work_dev, 2 * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMallocHost(&ctx->work_host, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMalloc(&ctx->work_dev, 3 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&ctx->work_host, 3 * sizeof(unsigned long long)) != cudaSuccess) {
         te_ctx_destroy(ctx);
         return TE_ECUDA;
     }
@@ -714,7 +740,7 @@ void te_ctx_destroy(te_ctx *ctx)
     DevBuf *bufs[] = {&ctx->ws_groups, &ctx->ws_members, &ctx->ws_cols,  &ctx->ws_acc,
                       &ctx->ws_keys,   &ctx->ws_perm,    &ctx->ws_stat,  &ctx->ws_dbg,
                       &ctx->ws_order,  &ctx->ws_ojobs,  &ctx->ws_cperm, &ctx->ws_gauss,
-                      &ctx->ws_vsort};
+                      &ctx->ws_vsort,  &ctx->ws_xval};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->q_dev) cudaFree(ctx->q_dev);

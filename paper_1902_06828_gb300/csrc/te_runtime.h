@@ -62,6 +62,7 @@ struct te_ctx {
     // grow-only device workspaces
     teksg::DevBuf ws_groups, ws_members, ws_cols, ws_acc, ws_keys, ws_perm, ws_stat, ws_dbg;
     teksg::DevBuf ws_order, ws_ojobs, ws_cperm, ws_gauss, ws_vsort;
+    teksg::DevBuf ws_xval;   // X-value rows of the TMA-staged lane kernel
     // pinned host staging
     void *pin = nullptr;
     size_t pin_cap = 0;
@@ -71,7 +72,7 @@ struct te_ctx {
     uint64_t pend_pair_evals = 0, pend_members = 0;
     struct te_server *server = nullptr;   // serving state (te_serve_*), created on demand
     std::mutex serve_start_mu;
-    unsigned long long *work_dev = nullptr;   // executed-work counter of the KSG kernel
+    unsigned long long *work_dev = nullptr;   // KSG kernel work counters [2], error flag [1]
     unsigned long long *work_host = nullptr;  // pinned copy
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     int prepared = 0;

@@ -83,7 +83,7 @@ def test_cancel_budget_and_timeout(env):
     big = te.Job(d, [(1, 1)], [(0, 0)], [(0, 1)], k=4, max_lag=5, n_surr=400, seed=1)
     huge = te.Job(d, [(1, 1)], [(0, 0)], [(0, 1)], k=4, max_lag=5, n_surr=4000, seed=1)
     with pytest.raises(te.TEError, match="TE_EBUSY"):
-        te.te_serve_submit(ctx, huge)          # 8 S N bytes > 256 MiB
+        te.te_serve_submit(ctx, huge)          # about 12 S N bytes > 256 MiB
     t1 = te.te_serve_submit(ctx, big)
     t2 = te.te_serve_submit(ctx, big)          # waits behind t1 (one job per batch)
     te.te_serve_cancel(ctx, t2)
