@@ -899,21 +899,29 @@ __global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
 
     // d_Z and d_YZ of the live queries against the 8 points of the chunk at c;
     // lane = (query a, point u); masked pairs (past N, self, Theiler band) = +inf.
-    // Returns live4 without the queries whose 8 points all lie at or beyond the
-    // query's bound in the pass's shared subspace (d_YZ in pass 1, d_Z in pass
-    // 2): with the bound >= every member's threshold or eps, no member can insert
-    // or count one of them.
+    // Returns a byte per query (byte a nonzero: query a stays live): live4
+    // without the queries whose 8 points all lie at or beyond the query's bound
+    // in the pass's shared subspace (d_YZ in pass 1, d_Z in pass 2); with the
+    // bound >= every member's threshold or eps, no member can insert or count
+    // one of them.
     auto chunk_dist = [&](int j0, int c, unsigned live4, bool pass1) {
         const int a = lane >> 3, u = lane & 7;
         float dzv = -CUDART_INF_F, dyzv = -CUDART_INF_F;
         bool keep = false;
         if ((live4 >> a) & 1u) {
             const float *qc = s_q + (warp * LQ + a) * dyz;
+            const float *tp = t_yz + c + u;
+#pragma unroll 4
             for (int d = dy; d < dyz; ++d)
-                dzv = fmaxf(dzv, fabsf(__fsub_rn(qc[d], t_yz[d * jt + c + u])));
-            dyzv = dzv;
-            for (int d = 0; d < dy; ++d)
-                dyzv = fmaxf(dyzv, fabsf(__fsub_rn(qc[d], t_yz[d * jt + c + u])));
+                dzv = fmaxf(dzv, fabsf(__fsub_rn(qc[d], tp[d * jt])));
+            if (dy == 1) {
+                dyzv = fmaxf(dzv, fabsf(__fsub_rn(qc[0], tp[0])));
+            } else {
+                dyzv = dzv;
+#pragma unroll 2
+                for (int d = 0; d < dy; ++d)
+                    dyzv = fmaxf(dyzv, fabsf(__fsub_rn(qc[d], tp[d * jt])));
+            }
             const int j = j0 + c + u;
             const int qp = min(qbase + a, N - 1);
             const int gap = j > qp ? j - qp : qp - j;
@@ -928,11 +936,8 @@ __global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
         const unsigned kb = __ballot_sync(0xffffffffu, keep);
         s_dz[(warp * LQ + a) * 8 + u] = dzv;
         s_dyz[(warp * LQ + a) * 8 + u] = dyzv;
-        unsigned out = 0;
-#pragma unroll
-        for (int b = 0; b < LQ; ++b) out |= ((kb >> (8 * b)) & 0xFFu) ? (1u << b) : 0u;
         __syncwarp();
-        return out;
+        return kb;
     };
 
     const int ntiles = (N + jt - 1) / jt;
@@ -984,16 +989,16 @@ __global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
             while (rest) {
                 const int c = (__ffs(rest) - 1) * JC;
                 rest &= rest - 1;
-                unsigned live4 = (s_bits[warp * wpt + (c >> 6)] >> (4 * ((c >> 3) & 7))) & 0xFu;
+                const unsigned live4 = (s_bits[warp * wpt + (c >> 6)] >> (4 * ((c >> 3) & 7))) & 0xFu;
                 if (!live4) continue;
-                live4 = chunk_dist(j0, c, live4, true);
-                if (!live4) continue;
+                const unsigned kb = chunk_dist(j0, c, live4, true);
+                if (!kb) continue;
                 float xv[MS][JC];
 #pragma unroll
                 for (int q = 0; q < MS; ++q) load_x(c, q, xv[q]);
 #pragma unroll
                 for (int a = 0; a < LQ; ++a) {
-                    if (!((live4 >> a) & 1u)) continue;
+                    if (!((kb >> (8 * a)) & 0xFFu)) continue;
                     ++executed1;
                     float dv[JC];
                     load8(s_dyz + (warp * LQ + a) * 8, dv);
@@ -1108,16 +1113,16 @@ __global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
         while (rest) {
             const int c = (__ffs(rest) - 1) * JC;
             rest &= rest - 1;
-            unsigned live4 = (s_bits[warp * wpt + (c >> 6)] >> (4 * ((c >> 3) & 7))) & 0xFu;
+            const unsigned live4 = (s_bits[warp * wpt + (c >> 6)] >> (4 * ((c >> 3) & 7))) & 0xFu;
             if (!live4) continue;
-            live4 = chunk_dist(j0, c, live4, false);
-            if (!live4) continue;
+            const unsigned kb = chunk_dist(j0, c, live4, false);
+            if (!kb) continue;
             float xv[MS][JC];
 #pragma unroll
             for (int q = 0; q < MS; ++q) load_x(c, q, xv[q]);
 #pragma unroll
             for (int a = 0; a < LQ; ++a) {
-                if (!((live4 >> a) & 1u)) continue;
+                if (!((kb >> (8 * a)) & 0xFFu)) continue;
                 ++executed2;
                 float zv[JC], yv[JC];
                 load8(s_dz + (warp * LQ + a) * 8, zv);
