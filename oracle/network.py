@@ -137,8 +137,20 @@ def _remove(lst, item):
     return [v for v in lst if v != item]
 
 
+def _resolve_theiler(series, p: Params) -> Params:
+    """A negative window means automatic: the largest autocorrelation decay
+    time over the processes (Supporting Information, dynamic correlation
+    exclusion)."""
+    if p.theiler >= 0:
+        return p
+    from dataclasses import replace
+    from .theiler import theiler_window
+    return replace(p, theiler=theiler_window(series))
+
+
 def infer_target(series, target: int, p: Params) -> TargetResult:
     series = np.ascontiguousarray(series, dtype=np.float32)
+    p = _resolve_theiler(series, p)
     n_proc, T = series.shape
     t0 = max(p.max_lag_target, p.max_lag_sources)
     N = T - t0
@@ -258,6 +270,7 @@ def fdr_bh(pvals, alpha: float):
 
 def infer_network(series, p: Params, targets=None):
     series = np.ascontiguousarray(series, dtype=np.float32)
+    p = _resolve_theiler(series, p)
     n_proc = series.shape[0]
     targets = list(range(n_proc)) if targets is None else list(targets)
     results = [infer_target(series, t, p) for t in targets]

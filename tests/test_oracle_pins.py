@@ -371,3 +371,74 @@ def test_gauss_population_closed_form():
                                     max_lag=0)[0])
     want = _gauss_cmi_closed(cov)
     assert abs(np.mean(vals) - want) < 3 * np.std(vals, ddof=1) / math.sqrt(len(vals)) + 2e-4
+
+
+# ---- Theiler-window heuristic: autocorrelation decay time ---------------------
+# (Supporting Information, dynamic correlation exclusion: shortest shift at
+# which the autocorrelation drops by 1/e)
+
+from oracle import theiler as oth
+
+
+def test_inv_e_constant_is_nearest_double():
+    import sympy
+    exact = sympy.exp(-1).evalf(50)
+    assert abs(sympy.Float(oth.INV_E, 50) - exact) <= sympy.Float(2.0 ** -55, 50)
+
+
+def test_decay_time_linear_ramp_by_hand():
+    # x = 1..8: deviations -3.5..3.5, sum of squares 42; lag-1 products sum to
+    # 26.25 (r = 0.625 > 1/e), lag-2 products to 11.5 (r = 0.274 <= 1/e)
+    x = np.arange(1, 9, dtype=np.float32)
+    assert oth.acf(x, 1) == 26.25 / 42
+    assert oth.acf(x, 2) == 11.5 / 42
+    assert oth.autocorr_decay_time(x) == 2
+
+
+@pytest.mark.parametrize("phi,tau", [(0.5, 2), (0.8, 5), (0.9, 10)])
+def test_decay_time_ar1_closed_form(phi, tau):
+    # AR(1) has r(t) = phi^t, so the decay time is the first t with phi^t <= 1/e
+    # (every case keeps phi^t at least 0.019 away from 1/e, over 6 standard
+    # errors of the sample autocorrelation at T = 10^6)
+    from scipy.signal import lfilter
+    assert phi ** (tau - 1) > math.exp(-1) + 0.019 and phi ** tau < math.exp(-1) - 0.019
+    rng = np.random.default_rng(int(phi * 100))
+    x = lfilter([1.0], [1.0, -phi], rng.normal(size=1_000_000))
+    assert oth.autocorr_decay_time(x.astype(np.float32)) == tau
+
+
+def test_decay_time_sine_closed_form():
+    # r(t) -> cos(2 pi t / P) for a long sine: first t with cos <= 1/e at P = 50
+    # is 10 (cos = 0.309; t = 9 gives 0.426)
+    t = np.arange(100_000)
+    x = np.sin(2 * np.pi * t / 50).astype(np.float32)
+    assert oth.autocorr_decay_time(x) == 10
+
+
+def test_decay_time_white_noise_and_constant():
+    rng = np.random.default_rng(3)
+    assert oth.autocorr_decay_time(rng.normal(size=5000).astype(np.float32)) == 1
+    assert oth.autocorr_decay_time(np.full(100, 2.5, np.float32)) == 1
+
+
+def test_theiler_window_is_max_over_processes():
+    x = np.stack([np.arange(1, 9), np.arange(8, 0, -1), [1, -1] * 4]).astype(np.float32)
+    assert [oth.autocorr_decay_time(r) for r in x] == [2, 2, 1]
+    assert oth.theiler_window(x) == 2
+
+
+def test_network_automatic_theiler_equals_explicit_window():
+    # an automatic window is the same run as the explicit largest decay time
+    rng = np.random.default_rng(12)
+    from scipy.signal import lfilter
+    s = np.stack([lfilter([1.0], [1.0, -0.7], rng.normal(size=160)) for _ in range(3)])
+    s[1, 1:] += 0.8 * s[0, :-1]
+    s = synth.standardise_jitter(s, 12).astype(np.float32)
+    w = oth.theiler_window(s)
+    assert w >= 2
+    kw = dict(k=4, max_lag_target=1, max_lag_sources=1, n_surr=20, alpha_max=0.1,
+              alpha_min=0.1, alpha_omnibus=0.1, seed=3)
+    auto = onet.infer_network(s, onet.Params(theiler=-1, **kw))
+    expl = onet.infer_network(s, onet.Params(theiler=w, **kw))
+    assert np.array_equal(auto[0], expl[0])
+    assert [r.sel_sources for r in auto[1]] == [r.sel_sources for r in expl[1]]
