@@ -180,10 +180,24 @@ te_status cmi_gauss(te_ctx *ctx, const te_data *data, const te_var *x, int32_t d
                     const te_var *y, int32_t dy, const te_var *z, int32_t dz,
                     const te_ksg_params *params, double *out_cmi, double *out_err_bound);
 
+/* ---- Theiler-window heuristic ---------------------------------------------- */
+
+/* Autocorrelation decay time (Supporting Information, dynamic correlation
+ * exclusion, the heuristic for the Theiler window): the smallest shift
+ * tau >= 1 at which the biased sample autocorrelation of process `proc`,
+ * r(tau) = sum_{t < T - tau} (x_t - m)(x_{t+tau} - m) / sum_t (x_t - m)^2 with m
+ * the series mean, FP64 sums, is <= 1/e (the FP64 number nearest to e^-1);
+ * T - 1 if it never is, 1 for a constant series.  proc = -1 gives the largest
+ * decay time over all processes.  Blocks until the result is on the host.
+ * Errors: TE_EINVAL (proc out of range, T < 2), TE_ENOMEM, TE_ECUDA. */
+te_status te_autocorr_decay(te_ctx *ctx, const te_data *data, int32_t proc, int32_t *out_tau);
+
 /* ---- greedy network inference -------------------------------------------- */
 
 typedef struct {
-    int32_t k, theiler;            /* estimator parameters, as te_ksg_params */
+    int32_t k, theiler;            /* estimator parameters, as te_ksg_params; theiler < 0:
+                                      automatic, the largest autocorrelation decay time over
+                                      the processes (te_autocorr_decay with proc = -1) */
     int32_t max_lag_target;        /* l_target >= 1 */
     int32_t max_lag_sources;       /* l_sources >= 1 */
     int32_t n_surr;                /* S; every test needs S * alpha > 1 */
@@ -215,6 +229,7 @@ typedef struct {
     int32_t *min_lag;              /* [n_proc * n_proc], smallest selected lag, 0 = no link */
     uint64_t n_estimates;          /* total CMI estimates */
     double seconds;                /* wall time of the inference */
+    int32_t theiler;               /* Theiler window the estimates used */
 } te_network_result;
 
 /*

@@ -27,7 +27,7 @@ from ._abi import TE_MAX_DIMS, TE_MAX_K  # noqa: F401
 __all__ = ["Context", "Data", "TEError", "te_data_create", "cmi_ksg", "cmi_ksg_debug",
            "cmi_ksg_batch", "te_network_infer", "te_get_stats", "Job", "library_path",
            "cmi_ksg_static", "cmi_gauss", "te_serve_start", "te_serve_submit", "te_serve_poll",
-           "te_serve_cancel", "te_serve_stop", "te_serve_get_stats"]
+           "te_serve_cancel", "te_serve_stop", "te_serve_get_stats", "te_autocorr_decay"]
 
 
 class TEError(RuntimeError):
@@ -312,13 +312,22 @@ def te_network_infer(ctx: Context, data: Data, *, k=4, theiler=0, max_lag_target
                 omnibus_tested=bool(t.omnibus_tested), significant=bool(t.significant),
                 n_estimates=int(t.n_estimates)))
         return dict(adjacency=adj, min_lag=lag, targets=tlist, n_estimates=int(R.n_estimates),
-                    seconds=R.seconds)
+                    seconds=R.seconds, theiler=int(R.theiler))
     finally:
         ctx._lib.te_network_result_free(res)
 
 
 def te_get_stats(ctx: Context) -> dict:
     return ctx.stats()
+
+
+def te_autocorr_decay(ctx: Context, data: Data, proc: int = -1) -> int:
+    """Autocorrelation decay time of one process (or the largest over all
+    with proc = -1): the Theiler-window heuristic."""
+    out = C.c_int32()
+    st = ctx._lib.te_autocorr_decay(ctx._h, data._h, int(proc), C.byref(out))
+    _check(ctx._h, st)
+    return int(out.value)
 
 
 def _job_struct(j, keep):

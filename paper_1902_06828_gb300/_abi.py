@@ -55,7 +55,7 @@ class NetworkResult(C.Structure):
     _fields_ = [("n_proc", C.c_int32), ("n_targets", C.c_int32),
                 ("targets", C.POINTER(TargetResult)), ("adjacency", C.POINTER(C.c_uint8)),
                 ("min_lag", C.POINTER(C.c_int32)), ("n_estimates", C.c_uint64),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("theiler", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -97,6 +97,7 @@ SIGNATURES = {
     "te_network_infer": (C.c_int, [_P, _P, C.POINTER(InferParams),
                                    C.POINTER(C.POINTER(NetworkResult))]),
     "te_network_result_free": (None, [C.POINTER(NetworkResult)]),
+    "te_autocorr_decay": (C.c_int, [_P, _P, _I32, C.POINTER(C.c_int32)]),
     "te_get_stats": (C.c_int, [_P, C.POINTER(Stats)]),
     "te_serve_start": (C.c_int, [_P, C.POINTER(ServeConfig)]),
     "te_serve_submit": (C.c_int, [_P, C.POINTER(CmiJob), C.POINTER(C.c_uint64)]),

@@ -112,13 +112,19 @@ te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_para
         ctx->err.clear();
         if (!data || !params || !out) return fail(ctx, TE_EINVAL, "NULL argument");
         if (data->ctx != ctx) return fail(ctx, TE_EINVAL, "data belongs to another context");
-        const te_infer_params P = *params;
+        te_infer_params P = *params;
         const int n_proc = data->n_proc, T = data->T;
         const int S = P.n_surr;
         if (P.max_lag_target < 1 || P.max_lag_sources < 1)
             return fail(ctx, TE_EINVAL, "max lags must be >= 1");
         if (P.k < 1 || P.k > TE_MAX_K) return fail(ctx, TE_EINVAL, "k must be in 1..16");
-        if (P.theiler < 0) return fail(ctx, TE_EINVAL, "theiler window must be >= 0");
+        if (P.theiler < 0) {   // automatic window: largest decay time over the processes
+            CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+            int32_t w = 0;
+            te_status st = autocorr_decay(ctx, data, -1, &w);
+            if (st) return st;
+            P.theiler = w;
+        }
         if (S < 1) return fail(ctx, TE_EINVAL, "n_surr must be >= 1");
         const double alphas[4] = {P.alpha_max, P.alpha_min, P.alpha_omnibus, P.alpha_seq};
         for (int a = 0; a < (P.seq_test ? 4 : 3); ++a)
@@ -375,6 +381,7 @@ te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_para
         }
         R->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start)
                          .count();
+        R->theiler = P.theiler;
         *out = R;
         return TE_OK;
     } catch (const std::bad_alloc &) {

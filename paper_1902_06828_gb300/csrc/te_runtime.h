@@ -88,6 +88,8 @@ namespace teksg {
     } while (0)
 
 te_status fail(te_ctx *ctx, te_status st, const std::string &msg);
+// largest autocorrelation decay time over process `proc` (>= 0) or all (-1)
+te_status autocorr_decay(te_ctx *ctx, const te_data *data, int32_t proc, int32_t *out_tau);
 te_status cuda_fail(te_ctx *ctx, cudaError_t e, const char *what);
 
 te_status ensure_dev(te_ctx *ctx, DevBuf &b, size_t bytes);
