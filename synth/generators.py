@@ -19,7 +19,8 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["er_graph", "var_chain3", "var_er", "clm_er", "standardise_jitter", "independent",
-           "gaussian_cmi_data", "workload_chain3", "workload_var10", "workload_clm100"]
+           "gaussian_cmi_data", "workload_chain3", "workload_var10", "workload_clm100",
+           "var_paper", "clm_paper"]
 
 
 def er_graph(n: int, p: float, rng) -> np.ndarray:
@@ -132,6 +133,63 @@ def clm_er(n: int = 100, T: int = 10000, seed: int = 1, p: float | None = None, 
                 a += (1.0 - self_w) * m
             v = 4.0 * a * (1.0 - a) + eta[t, i]
             x[t, i] = v - np.floor(v)
+    return x[burn:].T.copy(), adj, lags
+
+
+def _paper_couplings(n: int, p: float, rng, max_lag: int = 5, total: float = 0.4):
+    """ER topology with link probability p; every source of a target gets one
+    random lag in 1..max_lag and the same weight, the weights of a target
+    summing to `total`.  Returns (adjacency, lags, weights[src, tgt])."""
+    adj = er_graph(n, p, rng)
+    lags = np.zeros((n, n), np.int32)
+    wts = np.zeros((n, n))
+    for t in range(n):
+        srcs = np.nonzero(adj[:, t])[0]
+        for s_ in srcs:
+            lags[s_, t] = int(rng.integers(1, max_lag + 1))
+            wts[s_, t] = total / len(srcs)
+    return adj, lags, wts
+
+
+def var_paper(n: int, T: int, seed: int, p: float | None = None, beta: float = 0.5,
+              noise_sd: float = 0.1, burn: int = 1000, max_lag: int = 5):
+    """The validation VAR of the paper (Methods, "Vector autoregressive
+    process"): Y_t = beta Y_{t-1} + sum_X alpha_X X_{t - l_X} + eta_t with
+    beta = 0.5, one random lag l_X in 1..5 per source, equal cross-couplings
+    summing to 0.4 per target, eta ~ N(0, 0.1^2); ER topology with p = 3 / N.
+    Returns (float64 [n][T], adjacency, lags)."""
+    rng = np.random.default_rng(seed)
+    adj, lags, wts = _paper_couplings(n, 3.0 / n if p is None else p, rng, max_lag)
+    coef = np.zeros((max_lag, n, n))
+    for i in range(n):
+        coef[0, i, i] = beta
+    for s_ in range(n):
+        for t in range(n):
+            if adj[s_, t]:
+                coef[lags[s_, t] - 1, t, s_] += wts[s_, t]
+    return _simulate_var(coef, T, noise_sd, rng, burn), adj, lags
+
+
+def clm_paper(n: int, T: int, seed: int, p: float | None = None, beta: float = 0.5,
+              noise_sd: float = 0.1, burn: int = 1000, max_lag: int = 5):
+    """The validation coupled logistic maps of the paper (Methods, "Coupled
+    logistic maps process"): a_t = beta Y_{t-1} + sum_X alpha_X X_{t - l_X}
+    with the lags and couplings of var_paper, Y_t = (4 a_t (1 - a_t) + eta_t)
+    mod 1.  Returns (float64 [n][T], adjacency, lags)."""
+    rng = np.random.default_rng(seed)
+    adj, lags, wts = _paper_couplings(n, 3.0 / n if p is None else p, rng, max_lag)
+    total = T + burn
+    x = np.zeros((total, n))
+    x[:max_lag] = rng.random((max_lag, n))
+    eta = rng.normal(0.0, noise_sd, size=(total, n))
+    srcs = [np.nonzero(adj[:, t])[0] for t in range(n)]
+    for t in range(max_lag, total):
+        a = beta * x[t - 1]
+        for i in range(n):
+            for s_ in srcs[i]:
+                a[i] += wts[s_, i] * x[t - lags[s_, i], s_]
+        v = 4.0 * a * (1.0 - a) + eta[t]
+        x[t] = v - np.floor(v)
     return x[burn:].T.copy(), adj, lags
 
 

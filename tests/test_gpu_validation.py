@@ -1,0 +1,44 @@
+"""GPU: the validation harness on small networks equals the same harness
+applied to the network oracle's inferred networks."""
+import numpy as np
+import pytest
+
+from oracle import network as onet
+from paper_1902_06828_gb300 import validation as val
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1902_06828_gb300 as te
+    c = te.Context(0)
+    yield c
+    c.close()
+
+
+def _oracle_adj(series, alpha, n_surr, seed):
+    p = onet.Params(k=4, max_lag_target=5, max_lag_sources=5, n_surr=n_surr, alpha_max=alpha,
+                    alpha_min=alpha, alpha_omnibus=alpha, seed=seed)
+    return onet.infer_network(series, p)[0]
+
+
+def test_e1_scores_match_oracle(ctx):
+    rows = val.run_e1(ctx, "var", sizes=(5,), lengths=(700,), n_sims=1, alpha=0.1, n_surr=40,
+                      seed=3, out=lambda s: None)
+    series, adj = val._network("var", 5, 700, 3 + 5)
+    want = val.scores(adj, _oracle_adj(series, 0.1, 40, 3))
+    got = rows[0]
+    for key in ("tp", "fp", "tn", "fn"):
+        assert got[key] == want[key]
+
+
+def test_e2_false_positive_rate_matches_oracle(ctx):
+    rows = val.run_e2(ctx, "var", sizes=(4,), alphas=(0.1,), n_sims=2, T=500, n_surr=40, seed=7,
+                      out=lambda s: None)
+    rates = []
+    for s in range(2):
+        series, adj = val._network("var", 4, 500, 7 + 1000 * s + 4, empty=True)
+        assert adj.sum() == 0
+        rates.append(val.fpr_target(_oracle_adj(series, 0.1, 40, 7 + s)))
+    assert rows[0]["fpr_target"] == float(np.mean(rates))
