@@ -27,6 +27,8 @@ notes):
     (process, lag) ascending in steps 3 and the sequential test);
   * one permutation per (stage, iteration, surrogate) is shared by every
     candidate of that test (the classic maximum-statistic permutation test);
+    with indep_surr each candidate draws its own (counter s + c * 2^32 for
+    candidate c of the test in canonical order);
   * pruning repeats until the minimum contribution IS significant or the set
     is empty (the paper's "until ... not significant" contradicts step b);
   * the minimum-statistic p-value uses the same direction as the maximum test;
@@ -63,6 +65,7 @@ class Params:
     fdr: bool = False
     alpha_fdr: float = 0.05
     seed: int = 0
+    indep_surr: bool = False
     n_threads: int | None = None
 
 
@@ -80,9 +83,24 @@ class TargetResult:
     trace: list = field(default_factory=list)   # (stage, iter, cands, keys, null, p, decision)
 
 
-def _perms(p: Params, target: int, stage: int, it: int, N: int):
-    return np.stack([ksg.permutation(p.seed, target, stage, it, s, N)
+def _perms(p: Params, target: int, stage: int, it: int, N: int, c: int = 0):
+    """Surrogate permutations of a test; with independent surrogates,
+    candidate c (canonical order, from 0) draws surrogate s with the counter
+    s + c * 2^32 (candidate 0 keeps the shared permutations)."""
+    off = (c << 32) if p.indep_surr else 0
+    return np.stack([ksg.permutation(p.seed, target, stage, it, s + off, N)
                      for s in range(1, p.n_surr + 1)]).astype(np.int32)
+
+
+def _shared_z_keys(series, target, cand, z, p: Params, t0, stage, it, N):
+    """Keys of single-variable candidates that share one conditioning set."""
+    if not p.indep_surr:
+        return _group_keys(series, target, [[c] for c in cand], z, p, t0,
+                           _perms(p, target, stage, it, N))
+    keys = []
+    for ci, c in enumerate(cand):
+        keys += _group_keys(series, target, [[c]], z, p, t0, _perms(p, target, stage, it, N, ci))
+    return keys
 
 
 def _group_keys(series, target, cands_x, z, p: Params, t0, perms):
@@ -162,8 +180,7 @@ def infer_target(series, target: int, p: Params) -> TargetResult:
     sel_y: list = []
     it = 0
     while cand:
-        perms = _perms(p, target, STAGE_TARGET, it, N)
-        keys = _group_keys(series, target, [[c] for c in cand], sel_y, p, t0, perms)
+        keys = _shared_z_keys(series, target, cand, sel_y, p, t0, STAGE_TARGET, it, N)
         res.n_estimates += len(cand) * (p.n_surr + 1)
         b, pval, sig, null = max_statistic_test(keys, p.alpha_max)
         res.trace.append((STAGE_TARGET, it, list(cand), keys, null, pval, sig))
@@ -178,8 +195,7 @@ def infer_target(series, target: int, p: Params) -> TargetResult:
     sel_x: list = []
     it = 0
     while cand:
-        perms = _perms(p, target, STAGE_SOURCES, it, N)
-        keys = _group_keys(series, target, [[c] for c in cand], sel_y + sel_x, p, t0, perms)
+        keys = _shared_z_keys(series, target, cand, sel_y + sel_x, p, t0, STAGE_SOURCES, it, N)
         res.n_estimates += len(cand) * (p.n_surr + 1)
         b, pval, sig, null = max_statistic_test(keys, p.alpha_max)
         res.trace.append((STAGE_SOURCES, it, list(cand), keys, null, pval, sig))
@@ -193,11 +209,11 @@ def infer_target(series, target: int, p: Params) -> TargetResult:
     it = 0
     while sel_x:
         order = sorted(sel_x)
-        perms = _perms(p, target, STAGE_PRUNE, it, N)
         keys = []
-        for c in order:
+        for ci, c in enumerate(order):
             rest = [v for v in order if v != c]
-            keys += _group_keys(series, target, [[c]], sel_y + rest, p, t0, perms)
+            keys += _group_keys(series, target, [[c]], sel_y + rest, p, t0,
+                                _perms(p, target, STAGE_PRUNE, it, N, ci))
         res.n_estimates += len(order) * (p.n_surr + 1)
         w, pval, sig, null = min_statistic_test(keys, p.alpha_min)
         res.trace.append((STAGE_PRUNE, it, list(order), keys, null, pval, sig))
@@ -227,11 +243,11 @@ def infer_target(series, target: int, p: Params) -> TargetResult:
     # Optional step-down stage
     if p.seq_test and sel_x:
         order = sorted(sel_x)
-        perms = _perms(p, target, STAGE_SEQ, 0, N)
         keys = []
-        for c in order:
+        for ci, c in enumerate(order):
             rest = [v for v in order if v != c]
-            keys += _group_keys(series, target, [[c]], sel_y + rest, p, t0, perms)
+            keys += _group_keys(series, target, [[c]], sel_y + rest, p, t0,
+                                _perms(p, target, STAGE_SEQ, 0, N, ci))
         res.n_estimates += len(order) * (p.n_surr + 1)
         S = p.n_surr
         null = [max(keys[c][s] for c in range(len(order))) for s in range(1, S + 1)]

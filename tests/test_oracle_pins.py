@@ -442,3 +442,24 @@ def test_network_automatic_theiler_equals_explicit_window():
     expl = onet.infer_network(s, onet.Params(theiler=w, **kw))
     assert np.array_equal(auto[0], expl[0])
     assert [r.sel_sources for r in auto[1]] == [r.sel_sources for r in expl[1]]
+
+
+def test_independent_surrogates_follow_their_definition():
+    # with indep_surr, every candidate's surrogate keys are the estimates with
+    # the permutation of counter s + c * 2^32, recomputed here one by one
+    w = synth.workload_chain3(T=300, seed=4, coupling=0.7)
+    s = w["series"]
+    kw = dict(k=4, max_lag_target=2, max_lag_sources=1, n_surr=12, alpha_max=0.1,
+              alpha_min=0.1, alpha_omnibus=0.1, seed=9)
+    r = onet.infer_target(s, 2, onet.Params(indep_surr=True, **kw))
+    stage, it, cands, keys, null, pval, sig = r.trace[0]
+    assert stage == onet.STAGE_TARGET and len(cands) == 2
+    N = s.shape[1] - 2
+    for ci, c in enumerate(cands):
+        for sidx in (1, 7, 12):
+            perm = ksg.permutation(9, 2, onet.STAGE_TARGET, it, sidx + (ci << 32), N)
+            o = ksg.cmi_ksg(s, [c], [(2, 0)], [], k=4, max_lag=2, perm=perm)
+            assert keys[ci][sidx] == o["key"]
+    # candidate 0 keeps the shared permutations; candidate 1 does not
+    shared = onet.infer_target(s, 2, onet.Params(**kw)).trace[0][3]
+    assert shared[0] == keys[0] and shared[1][0] == keys[1][0] and shared[1] != keys[1]
