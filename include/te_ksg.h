@@ -208,6 +208,11 @@ typedef struct {
     uint64_t seed;
     const int32_t *targets;        /* host array of target processes, or NULL = all */
     int32_t n_targets;
+    int32_t indep_surr;            /* 0: one permutation per (test, surrogate) shared by the
+                                      test's candidates; 1: each candidate c of a test (canonical
+                                      order, from 0) draws its own, surrogate s keyed by
+                                      s + c * 2^32 (Statistical tests, Maximum statistic test a:
+                                      surrogates generated for each candidate) */
 } te_infer_params;
 
 typedef struct {

@@ -279,7 +279,7 @@ def cmi_ksg_batch(ctx: Context, jobs, return_keys=False):
 def te_network_infer(ctx: Context, data: Data, *, k=4, theiler=0, max_lag_target=5,
                      max_lag_sources=5, n_surr=200, alpha_max=0.05, alpha_min=0.05,
                      alpha_omnibus=0.05, alpha_seq=0.05, seq_test=False, fdr=False,
-                     alpha_fdr=0.05, seed=0, targets=None) -> dict:
+                     alpha_fdr=0.05, seed=0, targets=None, indep_surr=False) -> dict:
     """Greedy multivariate TE network inference; returns a dict with the
     adjacency [src, tgt], min lags, per-target selections and counters."""
     tarr = None
@@ -290,7 +290,8 @@ def te_network_infer(ctx: Context, data: Data, *, k=4, theiler=0, max_lag_target
     P = _abi.InferParams(int(k), int(theiler), int(max_lag_target), int(max_lag_sources),
                          int(n_surr), float(alpha_max), float(alpha_min), float(alpha_omnibus),
                          float(alpha_seq), int(bool(seq_test)), int(bool(fdr)), float(alpha_fdr),
-                         int(seed), C.cast(tarr, C.POINTER(C.c_int32)) if tarr else None, nt)
+                         int(seed), C.cast(tarr, C.POINTER(C.c_int32)) if tarr else None, nt,
+                         int(bool(indep_surr)))
     res = C.POINTER(_abi.NetworkResult)()
     st = ctx._lib.te_network_infer(ctx._h, data._h, C.byref(P), C.byref(res))
     _check(ctx._h, st)

@@ -154,7 +154,8 @@ inline size_t ksg_smem_bytes(int rows_t, int rows_q, int jt, int qt)
 // Fisher-Yates permutations of [0, n), one per surrogate s = s_first .. s_first +
 // n_perm - 1, keyed by SplitMix64 over (seed, target, stage, iter, s).
 cudaError_t launch_perms(int32_t *out, long long stride, int n, uint64_t seed, uint64_t target,
-                         uint64_t stage, uint64_t iter, int s_first, int n_perm, cudaStream_t st);
+                         uint64_t stage, uint64_t iter, uint64_t s_first, int n_perm,
+                         cudaStream_t st);
 
 // Many requests of launch_perms in one launch; request r writes n_perm
 // permutations of [0, n) at out (stride n) for s = s_first .. s_first+n_perm-1,

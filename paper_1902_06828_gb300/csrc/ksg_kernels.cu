@@ -1198,11 +1198,11 @@ __device__ __forceinline__ uint64_t sm64_next(uint64_t &s)
 __device__ __forceinline__ uint64_t sm64_once(uint64_t x) { return sm64_next(x); }
 
 __global__ void fisher_yates_kernel(int32_t *out, long long stride, int n, uint64_t seed,
-                                    uint64_t target, uint64_t stage, uint64_t iter, int s_first,
-                                    int in_smem)
+                                    uint64_t target, uint64_t stage, uint64_t iter,
+                                    uint64_t s_first, int in_smem)
 {
     extern __shared__ int32_t sperm[];
-    const uint64_t s = (uint64_t)(s_first + (int)blockIdx.x);
+    const uint64_t s = s_first + blockIdx.x;
     int32_t *p = in_smem ? sperm : out + (long long)blockIdx.x * stride;
     for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = i;
     __syncthreads();
@@ -1650,7 +1650,8 @@ cudaError_t encode_xval_map(CUtensorMap *map, const float *xval, long long pitch
 }
 
 cudaError_t launch_perms(int32_t *out, long long stride, int n, uint64_t seed, uint64_t target,
-                         uint64_t stage, uint64_t iter, int s_first, int n_perm, cudaStream_t st)
+                         uint64_t stage, uint64_t iter, uint64_t s_first, int n_perm,
+                         cudaStream_t st)
 {
     if (n_perm <= 0) return cudaSuccess;
     const size_t smem = (size_t)n * sizeof(int32_t);

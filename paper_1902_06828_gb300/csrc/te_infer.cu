@@ -170,7 +170,19 @@ te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_para
             if (active.empty()) break;
 
             // ---- build the round: perms, groups, stat requests ----
-            const size_t perm_elems = (size_t)active.size() * S * N;
+            // permutation sets per target: one shared by the test's candidates,
+            // or one per candidate with independent surrogates
+            std::vector<size_t> set_off(active.size() + 1, 0);
+            for (size_t r = 0; r < active.size(); ++r) {
+                const TargetState &t = ts[active[r]];
+                size_t nc = 1;
+                if (P.indep_surr) {
+                    if (t.stage == ST_TARGET || t.stage == ST_SOURCES) nc = t.cand.size();
+                    else if (t.stage == ST_PRUNE || t.stage == ST_SEQ) nc = t.sel_x.size();
+                }
+                set_off[r + 1] = set_off[r] + std::max<size_t>(nc, 1);
+            }
+            const size_t perm_elems = set_off.back() * S * N;
             if ((st = ensure_dev(ctx, ctx->ws_perm, perm_elems * 4))) return st;
             int32_t *perm = (int32_t *)ctx->ws_perm.p;
             std::vector<HostGroup> groups;
@@ -178,15 +190,21 @@ te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_para
             int n_out = 0, cnt_total = 0, orig_total = 0;
             for (size_t r = 0; r < active.size(); ++r) {
                 TargetState &t = ts[active[r]];
-                int32_t *pr = perm + r * (size_t)S * N;
+                int32_t *pr = perm + set_off[r] * (size_t)S * N;
                 const int iter = (t.stage == ST_OMNIBUS || t.stage == ST_SEQ) ? 0 : t.it;
-                CK(launch_perms(pr, N, N, P.seed, (uint64_t)t.target, (uint64_t)t.stage,
-                                (uint64_t)iter, 1, S, ctx->stream),
-                   "permutation launch");
-                ctx->stats.launches++;
+                const size_t n_sets = set_off[r + 1] - set_off[r];
+                for (size_t c = 0; c < n_sets; ++c) {
+                    CK(launch_perms(pr + c * (size_t)S * N, N, N, P.seed, (uint64_t)t.target,
+                                    (uint64_t)t.stage, (uint64_t)iter, 1 + ((uint64_t)c << 32),
+                                    S, ctx->stream),
+                       "permutation launch");
+                    ctx->stats.launches++;
+                }
                 const te_var ypres{t.target, 0};
+                // candidate `c0 + c` of the test uses permutation set c0 + c when
+                // every candidate has its own set, set 0 otherwise
                 auto add_group = [&](const std::vector<te_var> &z,
-                                     const std::vector<std::vector<te_var>> &xs) {
+                                     const std::vector<std::vector<te_var>> &xs, size_t c0) {
                     HostGroup g;
                     g.data = data;
                     g.max_lag = t0;
@@ -200,10 +218,13 @@ te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_para
                     const int nx = (int)xs.size();
                     for (const auto &x : xs) g.xvars.insert(g.xvars.end(), x.begin(), x.end());
                     for (int s = 0; s <= S; ++s)
-                        for (int c = 0; c < nx; ++c)
+                        for (int c = 0; c < nx; ++c) {
+                            const size_t set = n_sets > 1 ? c0 + (size_t)c : 0;
                             g.members.push_back(HostMember{
-                                c * g.dx, s == 0 ? nullptr : pr + (size_t)(s - 1) * N,
+                                c * g.dx,
+                                s == 0 ? nullptr : pr + (set * S + (size_t)(s - 1)) * N,
                                 n_out + c * (S + 1) + s});
+                        }
                     n_out += nx * (S + 1);
                     groups.push_back(std::move(g));
                 };
@@ -214,20 +235,21 @@ te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_para
                     if (t.stage == ST_SOURCES) z.insert(z.end(), t.sel_x.begin(), t.sel_x.end());
                     std::vector<std::vector<te_var>> xs;
                     for (const te_var &c : t.order) xs.push_back({c});
-                    add_group(z, xs);
+                    add_group(z, xs, 0);
                     t.mode = 0;
                 } else if (t.stage == ST_PRUNE || t.stage == ST_SEQ) {
                     t.order = sorted_vars(t.sel_x);
-                    for (const te_var &c : t.order) {
+                    for (size_t ci = 0; ci < t.order.size(); ++ci) {
+                        const te_var &c = t.order[ci];
                         std::vector<te_var> z = t.sel_y;
                         for (const te_var &o : t.order)
                             if (!var_eq(o, c)) z.push_back(o);
-                        add_group(z, {{c}});
+                        add_group(z, {{c}}, ci);
                     }
                     t.mode = t.stage == ST_PRUNE ? 1 : 0;
                 } else {  // omnibus
                     t.order = sorted_vars(t.sel_x);
-                    add_group(t.sel_y, {t.order});
+                    add_group(t.sel_y, {t.order}, 0);
                     t.mode = 0;
                 }
                 t.n_cand = t.stage == ST_OMNIBUS ? 1 : (int)t.order.size();

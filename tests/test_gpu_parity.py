@@ -291,6 +291,21 @@ def test_network_inference_matches_oracle(te, ctx, seq, fdr):
     assert g["n_estimates"] == sum(r.n_estimates for r in res_o)
 
 
+def test_network_independent_surrogates_match_oracle(te, ctx):
+    """Every test draws one permutation set per candidate (counter
+    s + c * 2^32); networks, p-values and keys equal the oracle's."""
+    x, adj, lags = synth.var_er(n=4, p=0.4, T=350, seed=6, lo=0.4, hi=0.7, max_lag=2)
+    s = synth.standardise_jitter(x, 6)
+    data = te.te_data_create(ctx, s)
+    kw = dict(k=4, max_lag_target=2, max_lag_sources=2, n_surr=30, alpha_max=0.1,
+              alpha_min=0.1, alpha_omnibus=0.1, alpha_seq=0.1, seq_test=True, seed=13,
+              indep_surr=True)
+    g = te.te_network_infer(ctx, data, **kw)
+    adj_o, res_o = onet.infer_network(s, onet.Params(**kw))
+    _compare_networks(g, adj_o, res_o)
+    assert g["n_estimates"] == sum(r.n_estimates for r in res_o)
+
+
 def test_network_targets_subset(te, ctx):
     w = synth.workload_chain3(T=600, seed=2, coupling=0.7)
     data = te.te_data_create(ctx, w["series"])
