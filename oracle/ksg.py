@@ -37,6 +37,8 @@ def lib():
         L.oracle_splitmix64_stream.restype = None
         L.oracle_permutation.argtypes = [u64, u64, u64, u64, u64, i32, P]
         L.oracle_permutation.restype = C.c_int
+        L.oracle_permutation_trials.argtypes = [u64, u64, u64, u64, u64, i32, i32, i32, P]
+        L.oracle_permutation_trials.restype = C.c_int
         L.oracle_ksg_cmi.argtypes = [P, i32, i32, i32, i32, P, i32, P, i32, P, i32, P, i32, i32,
                                      P, P, P, P, P, P, P]
         L.oracle_ksg_cmi.restype = C.c_int
@@ -95,6 +97,30 @@ def permutation(seed: int, target: int, stage: int, it: int, s: int, n: int) -> 
     if st:
         raise ValueError("oracle_permutation: bad arguments")
     return p
+
+
+def permutation_trials(seed: int, target: int, stage: int, it: int, s: int, R: int, n: int,
+                       mode: int) -> np.ndarray:
+    """Surrogate permutation of R pooled trials of n points: mode 0 shuffles
+    the trial order, mode 1 the samples inside each trial."""
+    p = np.empty(R * n, dtype=np.int32)
+    st = lib().oracle_permutation_trials(seed, target, stage, it, s, R, n, mode, _ptr(p))
+    if st:
+        raise ValueError("oracle_permutation_trials: bad arguments")
+    return p
+
+
+def pool_trials(series3, L: int) -> np.ndarray:
+    """Embedded, pooled view of a [n_proc][R][T] series for lags 0..L: row
+    p * (L + 1) + l holds X_p at lag l for the points t = L .. T - 1 of every
+    trial, trial by trial (R (T - L) points)."""
+    s = np.asarray(series3, dtype=np.float32)
+    n_proc, R, T = s.shape
+    out = np.empty((n_proc * (L + 1), R * (T - L)), dtype=np.float32)
+    for p in range(n_proc):
+        for l in range(L + 1):
+            out[p * (L + 1) + l] = s[p, :, L - l:T - l].reshape(-1)
+    return out
 
 
 def cmi_ksg(series, x, y, z, *, k=4, theiler=0, max_lag=None, perm=None, per_point=False):

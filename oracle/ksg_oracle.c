@@ -179,6 +179,49 @@ int oracle_permutation(uint64_t seed, uint64_t target, uint64_t stage, uint64_t 
     return OR_OK;
 }
 
+/* Surrogates of data with R replications (trials) of n points each, points
+ * pooled trial by trial (point r*n + t).  Methods, Statistical tests,
+ * surrogate paragraph: with enough replications the candidate's trial order
+ * is shuffled (mode 0: perm[r*n + t] = sigma[r]*n + t, sigma a Fisher-Yates
+ * shuffle of the R trials); otherwise its samples are shuffled inside each
+ * trial (mode 1: one Fisher-Yates shuffle per trial, trial 0 first, all drawn
+ * from one generator, so R = 1 gives oracle_permutation).  The generator
+ * state starts at the same key as oracle_permutation. */
+int oracle_permutation_trials(uint64_t seed, uint64_t target, uint64_t stage, uint64_t iter,
+                              uint64_t surr, int32_t R, int32_t n, int32_t mode, int32_t *perm)
+{
+    if (R < 1 || n < 1 || !perm || (mode != 0 && mode != 1)) return OR_EINVAL;
+    uint64_t state = oracle_perm_key(seed, target, stage, iter, surr);
+    if (mode == 0) {
+        int32_t *sigma = (int32_t *)malloc(sizeof(int32_t) * (size_t)R);
+        if (!sigma) return OR_EINVAL;
+        for (int32_t r = 0; r < R; ++r) sigma[r] = r;
+        for (int32_t i = R - 1; i >= 1; --i) {
+            uint64_t x = splitmix64_next(&state);
+            int32_t j = (int32_t)(((u128)x * (u128)(uint64_t)(i + 1)) >> 64);
+            int32_t t = sigma[i];
+            sigma[i] = sigma[j];
+            sigma[j] = t;
+        }
+        for (int32_t r = 0; r < R; ++r)
+            for (int32_t t = 0; t < n; ++t) perm[(size_t)r * n + t] = sigma[r] * n + t;
+        free(sigma);
+        return OR_OK;
+    }
+    for (int32_t r = 0; r < R; ++r) {
+        int32_t *b = perm + (size_t)r * n;
+        for (int32_t t = 0; t < n; ++t) b[t] = r * n + t;
+        for (int32_t i = n - 1; i >= 1; --i) {
+            uint64_t x = splitmix64_next(&state);
+            int32_t j = (int32_t)(((u128)x * (u128)(uint64_t)(i + 1)) >> 64);
+            int32_t t = b[i];
+            b[i] = b[j];
+            b[j] = t;
+        }
+    }
+    return OR_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Brute-force KSG CMI for one member                                        */
 /* ------------------------------------------------------------------------ */

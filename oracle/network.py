@@ -37,10 +37,18 @@ notes):
   * the optional step-down ("sequential") stage follows the footnote on
     step-down tests: candidates ordered by their contribution, largest first,
     tested against the null of the maximum over candidates; at the first
-    non-significant one it and all smaller ones are removed.
+    non-significant one it and all smaller ones are removed;
+  * a negative Theiler window selects the automatic one: the largest
+    autocorrelation decay time over the processes (oracle/theiler.py);
+  * replications (trials) are embedded trial by trial and pooled point by
+    point (t = L .. T - 1 of trial 0, then of trial 1, ...); their
+    surrogates shuffle the candidate's trial order when the R! orders cover
+    the S surrogates, else its samples inside each trial (Statistical tests,
+    surrogate paragraph); no Theiler window is defined across trials.
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -83,41 +91,63 @@ class TargetResult:
     trace: list = field(default_factory=list)   # (stage, iter, cands, keys, null, p, decision)
 
 
-def _perms(p: Params, target: int, stage: int, it: int, N: int, c: int = 0):
+@dataclass
+class _View:
+    """What the estimates of one target read: the estimator's series, the
+    target present as a variable, the first point t0, the point count N, the
+    map from a (process, lag) variable to the estimator's variable, and for
+    pooled replications (R trials of n points, surrogate mode) the trial
+    layout."""
+    series: np.ndarray
+    target: int
+    y: tuple
+    t0: int
+    N: int
+    vmap: object = None
+    trials: tuple | None = None
+
+
+def _perms(p: Params, v: _View, stage: int, it: int, c: int = 0):
     """Surrogate permutations of a test; with independent surrogates,
     candidate c (canonical order, from 0) draws surrogate s with the counter
-    s + c * 2^32 (candidate 0 keeps the shared permutations)."""
+    s + c * 2^32 (candidate 0 keeps the shared permutations).  Pooled
+    replications shuffle the trial order or the samples inside each trial."""
     off = (c << 32) if p.indep_surr else 0
-    return np.stack([ksg.permutation(p.seed, target, stage, it, s + off, N)
+    if v.trials is not None:
+        R_, n, mode = v.trials
+        return np.stack([ksg.permutation_trials(p.seed, v.target, stage, it, s + off, R_, n, mode)
+                         for s in range(1, p.n_surr + 1)]).astype(np.int32)
+    return np.stack([ksg.permutation(p.seed, v.target, stage, it, s + off, v.N)
                      for s in range(1, p.n_surr + 1)]).astype(np.int32)
 
 
-def _shared_z_keys(series, target, cand, z, p: Params, t0, stage, it, N):
+def _shared_z_keys(v: _View, cand, z, p: Params, stage, it):
     """Keys of single-variable candidates that share one conditioning set."""
     if not p.indep_surr:
-        return _group_keys(series, target, [[c] for c in cand], z, p, t0,
-                           _perms(p, target, stage, it, N))
+        return _group_keys(v, [[c] for c in cand], z, p, _perms(p, v, stage, it))
     keys = []
     for ci, c in enumerate(cand):
-        keys += _group_keys(series, target, [[c]], z, p, t0, _perms(p, target, stage, it, N, ci))
+        keys += _group_keys(v, [[c]], z, p, _perms(p, v, stage, it, ci))
     return keys
 
 
-def _group_keys(series, target, cands_x, z, p: Params, t0, perms):
+def _group_keys(v: _View, cands_x, z, p: Params, perms):
     """Keys for every candidate (each a list of X variables of equal length)
     against Y = target present given Z, identity and every surrogate.
     Returns int array [n_cand][1 + S] of Python ints."""
+    vm = v.vmap or (lambda u: tuple(u))
     n_c = len(cands_x)
     S = perms.shape[0]
     xs, pidx = [], []
     for c in cands_x:
-        xs.append(c)
+        xs.append([vm(u) for u in c])
         pidx.append(-1)
-        for s in range(S):
-            xs.append(c)
-            pidx.append(s)
-    keys, _, _ = ksg.cmi_ksg_batch(series, xs, [(target, 0)], z, perms=perms, perm_idx=pidx,
-                                   k=p.k, theiler=p.theiler, max_lag=t0, n_threads=p.n_threads)
+        for s_ in range(S):
+            xs.append([vm(u) for u in c])
+            pidx.append(s_)
+    z = [vm(u) for u in z]
+    keys, _, _ = ksg.cmi_ksg_batch(v.series, xs, [v.y], z, perms=perms, perm_idx=pidx,
+                                   k=p.k, theiler=p.theiler, max_lag=v.t0, n_threads=p.n_threads)
     return [keys[c * (S + 1):(c + 1) * (S + 1)] for c in range(n_c)]
 
 
@@ -166,12 +196,38 @@ def _resolve_theiler(series, p: Params) -> Params:
     return replace(p, theiler=theiler_window(series))
 
 
-def infer_target(series, target: int, p: Params) -> TargetResult:
-    series = np.ascontiguousarray(series, dtype=np.float32)
-    p = _resolve_theiler(series, p)
-    n_proc, T = series.shape
+def _trial_mode(mode, R_: int, S: int) -> int:
+    """0 = shuffle the trial order, 1 = shuffle inside trials; 'auto' takes
+    trial shuffling when the R! trial orders cover the S surrogates."""
+    if mode == "trials":
+        return 0
+    if mode == "within":
+        return 1
+    return 0 if math.factorial(R_) >= S else 1
+
+
+def infer_target(series, target: int, p: Params, trials=None) -> TargetResult:
+    """series: [n_proc][T], or with trials ('auto', 'trials' or 'within')
+    [n_proc][R][T] replications pooled point by point, each trial embedded on
+    its own."""
     t0 = max(p.max_lag_target, p.max_lag_sources)
-    N = T - t0
+    if trials is None:
+        series = np.ascontiguousarray(series, dtype=np.float32)
+        p = _resolve_theiler(series, p)
+        n_proc, T = series.shape
+        N = T - t0
+        v = _View(series, target, (target, 0), t0, N)
+    else:
+        s3 = np.ascontiguousarray(series, dtype=np.float32)
+        n_proc, R_, T = s3.shape
+        if p.theiler != 0:
+            raise ValueError("a Theiler window is not defined across pooled replications")
+        n = T - t0
+        N = R_ * n
+        pooled = ksg.pool_trials(s3, t0)
+        v = _View(pooled, target, (target * (t0 + 1), 0), 0, N,
+                  vmap=lambda u: (u[0] * (t0 + 1) + u[1], 0),
+                  trials=(R_, n, _trial_mode(trials, R_, p.n_surr)))
     q, _ = ksg.digamma_q(N + 1)
     res = TargetResult(target=target)
 
@@ -180,7 +236,7 @@ def infer_target(series, target: int, p: Params) -> TargetResult:
     sel_y: list = []
     it = 0
     while cand:
-        keys = _shared_z_keys(series, target, cand, sel_y, p, t0, STAGE_TARGET, it, N)
+        keys = _shared_z_keys(v, cand, sel_y, p, STAGE_TARGET, it)
         res.n_estimates += len(cand) * (p.n_surr + 1)
         b, pval, sig, null = max_statistic_test(keys, p.alpha_max)
         res.trace.append((STAGE_TARGET, it, list(cand), keys, null, pval, sig))
@@ -195,7 +251,7 @@ def infer_target(series, target: int, p: Params) -> TargetResult:
     sel_x: list = []
     it = 0
     while cand:
-        keys = _shared_z_keys(series, target, cand, sel_y + sel_x, p, t0, STAGE_SOURCES, it, N)
+        keys = _shared_z_keys(v, cand, sel_y + sel_x, p, STAGE_SOURCES, it)
         res.n_estimates += len(cand) * (p.n_surr + 1)
         b, pval, sig, null = max_statistic_test(keys, p.alpha_max)
         res.trace.append((STAGE_SOURCES, it, list(cand), keys, null, pval, sig))
@@ -212,8 +268,7 @@ def infer_target(series, target: int, p: Params) -> TargetResult:
         keys = []
         for ci, c in enumerate(order):
             rest = [v for v in order if v != c]
-            keys += _group_keys(series, target, [[c]], sel_y + rest, p, t0,
-                                _perms(p, target, STAGE_PRUNE, it, N, ci))
+            keys += _group_keys(v, [[c]], sel_y + rest, p, _perms(p, v, STAGE_PRUNE, it, ci))
         res.n_estimates += len(order) * (p.n_surr + 1)
         w, pval, sig, null = min_statistic_test(keys, p.alpha_min)
         res.trace.append((STAGE_PRUNE, it, list(order), keys, null, pval, sig))
@@ -225,8 +280,7 @@ def infer_target(series, target: int, p: Params) -> TargetResult:
     # Step 4: omnibus
     if sel_x:
         order = sorted(sel_x)
-        perms = _perms(p, target, STAGE_OMNIBUS, 0, N)
-        keys = _group_keys(series, target, [order], sel_y, p, t0, perms)[0]
+        keys = _group_keys(v, [order], sel_y, p, _perms(p, v, STAGE_OMNIBUS, 0))[0]
         res.n_estimates += p.n_surr + 1
         kstar = keys[0]
         cnt = sum(1 for v in keys[1:] if v > kstar)
@@ -246,8 +300,7 @@ def infer_target(series, target: int, p: Params) -> TargetResult:
         keys = []
         for ci, c in enumerate(order):
             rest = [v for v in order if v != c]
-            keys += _group_keys(series, target, [[c]], sel_y + rest, p, t0,
-                                _perms(p, target, STAGE_SEQ, 0, N, ci))
+            keys += _group_keys(v, [[c]], sel_y + rest, p, _perms(p, v, STAGE_SEQ, 0, ci))
         res.n_estimates += len(order) * (p.n_surr + 1)
         S = p.n_surr
         null = [max(keys[c][s] for c in range(len(order))) for s in range(1, S + 1)]
@@ -284,12 +337,13 @@ def fdr_bh(pvals, alpha: float):
     return rej
 
 
-def infer_network(series, p: Params, targets=None):
+def infer_network(series, p: Params, targets=None, trials=None):
     series = np.ascontiguousarray(series, dtype=np.float32)
-    p = _resolve_theiler(series, p)
+    if trials is None:
+        p = _resolve_theiler(series, p)
     n_proc = series.shape[0]
     targets = list(range(n_proc)) if targets is None else list(targets)
-    results = [infer_target(series, t, p) for t in targets]
+    results = [infer_target(series, t, p, trials) for t in targets]
     if p.fdr:
         tested = [r for r in results if r.omnibus_tested]
         rej = fdr_bh([r.omnibus_p for r in tested], p.alpha_fdr)

@@ -463,3 +463,76 @@ def test_independent_surrogates_follow_their_definition():
     # candidate 0 keeps the shared permutations; candidate 1 does not
     shared = onet.infer_target(s, 2, onet.Params(**kw)).trace[0][3]
     assert shared[0] == keys[0] and shared[1][0] == keys[1][0] and shared[1] != keys[1]
+
+
+# ---- replications (trials): pooled embedding and trial surrogates ------------
+
+_M64 = (1 << 64) - 1
+
+
+def _sm64_py(state):
+    """SplitMix64 written out in Python: (new state, output)."""
+    state = (state + 0x9E3779B97F4A7C15) & _M64
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return state, z ^ (z >> 31)
+
+
+def _fy_py(items, state):
+    """Fisher-Yates from the last position down, j = floor(r (i + 1) / 2^64)."""
+    a = list(items)
+    for i in range(len(a) - 1, 0, -1):
+        state, r = _sm64_py(state)
+        j = (r * (i + 1)) >> 64
+        a[i], a[j] = a[j], a[i]
+    return a, state
+
+
+def test_trial_permutations_follow_their_definition():
+    key = ksg.perm_key(11, 2, 1, 0, 5)
+    R, n = 6, 9
+    # mode 0: the trial order is a Fisher-Yates shuffle of the R trials
+    sigma, _ = _fy_py(range(R), key)
+    want = [sigma[r] * n + t for r in range(R) for t in range(n)]
+    assert ksg.permutation_trials(11, 2, 1, 0, 5, R, n, 0).tolist() == want
+    # mode 1: one shuffle per trial, trial 0 first, one continuing generator
+    state, want = key, []
+    for r in range(R):
+        blk, state = _fy_py(range(r * n, (r + 1) * n), state)
+        want += blk
+    assert ksg.permutation_trials(11, 2, 1, 0, 5, R, n, 1).tolist() == want
+    # one trial shuffled inside is the ordinary permutation
+    assert np.array_equal(ksg.permutation_trials(11, 2, 1, 0, 5, 1, 40, 1),
+                          ksg.permutation(11, 2, 1, 0, 5, 40))
+
+
+def test_pool_trials_layout_and_single_trial_estimate():
+    rng = np.random.default_rng(8)
+    s3 = rng.normal(size=(2, 3, 7)).astype(np.float32)
+    pooled = ksg.pool_trials(s3, 2)
+    assert pooled.shape == (6, 15)
+    # row p * 3 + l, point r * 5 + t holds process p of trial r at time 2 + t - l
+    for p in range(2):
+        for l in range(3):
+            for r in range(3):
+                for t in range(5):
+                    assert pooled[p * 3 + l, r * 5 + t] == s3[p, r, 2 + t - l]
+    # one trial: estimates on the pooled view equal the ordinary ones
+    w = synth.workload_chain3(T=300, seed=2, coupling=0.7)
+    one = w["series"][:, None, :]
+    pv = ksg.pool_trials(one, 2)
+    m = lambda v: [(p * 3 + l, 0) for p, l in v]
+    a = ksg.cmi_ksg(pv, m(w["x"]), m(w["y"]), m(w["z"]), k=4, max_lag=0)
+    b = ksg.cmi_ksg(w["series"], w["x"], w["y"], w["z"], k=4, max_lag=2)
+    assert a["key"] == b["key"]
+
+
+def test_network_with_one_trial_equals_ordinary_network():
+    w = synth.workload_chain3(T=260, seed=5, coupling=0.7)
+    kw = dict(k=4, max_lag_target=2, max_lag_sources=2, n_surr=20, alpha_max=0.1,
+              alpha_min=0.1, alpha_omnibus=0.1, seed=4)
+    adj1, r1 = onet.infer_network(w["series"], onet.Params(**kw))
+    adj2, r2 = onet.infer_network(w["series"][:, None, :], onet.Params(**kw), trials="within")
+    assert np.array_equal(adj1, adj2)
+    assert [t.trace for t in r1] == [t.trace for t in r2]
