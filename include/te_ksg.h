@@ -85,6 +85,23 @@ te_status te_data_create(te_ctx *ctx, const float *series, int32_t n_proc, int32
                          int series_on_device, te_data **out);
 void te_data_destroy(te_data *data);
 
+/* Replications (trials) of an experiment (Methods, problem statement: the
+ * replication number R; Statistical tests, surrogate paragraph).  `series`
+ * is float32 [n_proc][n_rep][T] row-major (host, or device if
+ * series_on_device).  Every trial is embedded on its own with the maximum
+ * lag L = max_lag and the trials are pooled point by point: the data set
+ * holds n_proc * (L + 1) rows of n_rep * (T - L) points, row p * (L + 1) + l
+ * being process p at lag l (point r * (T - L) + t = trial r, time L + t - l).
+ * te_network_infer takes such data with max(l_target, l_sources) == L and
+ * theiler == 0, enumerates candidates over the n_proc processes and draws
+ * trial surrogates (te_infer_params.surr_mode).  The single-estimate calls
+ * read the rows as processes: variable (p, l) is row p * (L + 1) + l at lag 0,
+ * with max_lag 0.
+ * Errors: TE_EINVAL (NULL pointers, n_rep < 1, T - max_lag < 2, more than
+ * 2^31 pooled values, a non-finite value), TE_ENOMEM, TE_ECUDA. */
+te_status te_data_create_trials(te_ctx *ctx, const float *series, int32_t n_proc, int32_t n_rep,
+                                int32_t T, int32_t max_lag, int series_on_device, te_data **out);
+
 /* ---- one KSG estimate and its surrogates ---------------------------------- */
 
 typedef struct {
@@ -213,6 +230,14 @@ typedef struct {
                                       order, from 0) draws its own, surrogate s keyed by
                                       s + c * 2^32 (Statistical tests, Maximum statistic test a:
                                       surrogates generated for each candidate) */
+    int32_t surr_mode;             /* data from te_data_create_trials only (Statistical tests,
+                                      surrogate paragraph): 0 = shuffle the candidate's trial
+                                      order when the n_rep! orders cover n_surr, else its samples
+                                      inside each trial; 1 = trial order; 2 = inside trials.
+                                      Trial order: point r*n + t reads trial sigma(r), sigma a
+                                      Fisher-Yates shuffle of the trials; inside trials: one
+                                      Fisher-Yates shuffle per trial, trial 0 first, all drawn
+                                      from one SplitMix64 stream keyed as the permutations */
 } te_infer_params;
 
 typedef struct {

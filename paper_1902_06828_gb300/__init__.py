@@ -27,7 +27,8 @@ from ._abi import TE_MAX_DIMS, TE_MAX_K  # noqa: F401
 __all__ = ["Context", "Data", "TEError", "te_data_create", "cmi_ksg", "cmi_ksg_debug",
            "cmi_ksg_batch", "te_network_infer", "te_get_stats", "Job", "library_path",
            "cmi_ksg_static", "cmi_gauss", "te_serve_start", "te_serve_submit", "te_serve_poll",
-           "te_serve_cancel", "te_serve_stop", "te_serve_get_stats", "te_autocorr_decay"]
+           "te_serve_cancel", "te_serve_stop", "te_serve_get_stats", "te_autocorr_decay",
+           "te_data_create_trials", "trial_var"]
 
 
 class TEError(RuntimeError):
@@ -149,6 +150,27 @@ def te_data_create(ctx: Context, series) -> Data:
     del keep
     _check(ctx._h, st)
     return Data(ctx, h, int(n_proc), int(T))
+
+
+def te_data_create_trials(ctx: Context, series, max_lag: int) -> Data:
+    """series: float32 [n_proc][n_rep][T] replications (numpy).  Each trial
+    is embedded with the maximum lag `max_lag` and the trials are pooled:
+    row p * (max_lag + 1) + l of the result is process p at lag l."""
+    a = np.ascontiguousarray(series, dtype=np.float32)
+    if a.ndim != 3:
+        raise TEError(_abi.TE_EINVAL, "series must be 3-D [n_proc][n_rep][T]")
+    n_proc, n_rep, T = a.shape
+    h = C.c_void_p()
+    st = ctx._lib.te_data_create_trials(ctx._h, C.c_void_p(a.ctypes.data), int(n_proc),
+                                        int(n_rep), int(T), int(max_lag), 0, C.byref(h))
+    _check(ctx._h, st)
+    return Data(ctx, h, int(n_proc) * (int(max_lag) + 1), int(n_rep) * (int(T) - int(max_lag)))
+
+
+def trial_var(proc: int, lag: int, max_lag: int) -> tuple:
+    """The row of pooled trial data holding process `proc` at `lag`, as a
+    variable for the single-estimate calls (lag 0, max_lag 0)."""
+    return (proc * (max_lag + 1) + lag, 0)
 
 
 def _params(k, theiler, max_lag, n_surr, seed, stream_tag):
@@ -279,7 +301,8 @@ def cmi_ksg_batch(ctx: Context, jobs, return_keys=False):
 def te_network_infer(ctx: Context, data: Data, *, k=4, theiler=0, max_lag_target=5,
                      max_lag_sources=5, n_surr=200, alpha_max=0.05, alpha_min=0.05,
                      alpha_omnibus=0.05, alpha_seq=0.05, seq_test=False, fdr=False,
-                     alpha_fdr=0.05, seed=0, targets=None, indep_surr=False) -> dict:
+                     alpha_fdr=0.05, seed=0, targets=None, indep_surr=False,
+                     surr_mode="auto") -> dict:
     """Greedy multivariate TE network inference; returns a dict with the
     adjacency [src, tgt], min lags, per-target selections and counters."""
     tarr = None
@@ -291,7 +314,7 @@ def te_network_infer(ctx: Context, data: Data, *, k=4, theiler=0, max_lag_target
                          int(n_surr), float(alpha_max), float(alpha_min), float(alpha_omnibus),
                          float(alpha_seq), int(bool(seq_test)), int(bool(fdr)), float(alpha_fdr),
                          int(seed), C.cast(tarr, C.POINTER(C.c_int32)) if tarr else None, nt,
-                         int(bool(indep_surr)))
+                         int(bool(indep_surr)), {"auto": 0, "trials": 1, "within": 2}[surr_mode])
     res = C.POINTER(_abi.NetworkResult)()
     st = ctx._lib.te_network_infer(ctx._h, data._h, C.byref(P), C.byref(res))
     _check(ctx._h, st)

@@ -40,7 +40,7 @@ class InferParams(C.Structure):
                 ("alpha_omnibus", C.c_double), ("alpha_seq", C.c_double),
                 ("seq_test", C.c_int32), ("fdr", C.c_int32), ("alpha_fdr", C.c_double),
                 ("seed", C.c_uint64), ("targets", C.POINTER(C.c_int32)),
-                ("n_targets", C.c_int32), ("indep_surr", C.c_int32)]
+                ("n_targets", C.c_int32), ("indep_surr", C.c_int32), ("surr_mode", C.c_int32)]
 
 
 class TargetResult(C.Structure):
@@ -98,6 +98,7 @@ SIGNATURES = {
                                    C.POINTER(C.POINTER(NetworkResult))]),
     "te_network_result_free": (None, [C.POINTER(NetworkResult)]),
     "te_autocorr_decay": (C.c_int, [_P, _P, _I32, C.POINTER(C.c_int32)]),
+    "te_data_create_trials": (C.c_int, [_P, _P, _I32, _I32, _I32, _I32, C.c_int, _P]),
     "te_get_stats": (C.c_int, [_P, C.POINTER(Stats)]),
     "te_serve_start": (C.c_int, [_P, C.POINTER(ServeConfig)]),
     "te_serve_submit": (C.c_int, [_P, C.POINTER(CmiJob), C.POINTER(C.c_uint64)]),

@@ -157,6 +157,13 @@ cudaError_t launch_perms(int32_t *out, long long stride, int n, uint64_t seed, u
                          uint64_t stage, uint64_t iter, uint64_t s_first, int n_perm,
                          cudaStream_t st);
 
+// Surrogates of R pooled trials of n points (R * n ints per surrogate, n_perm
+// of them at out): mode 0 shuffles the trial order, mode 1 the points inside
+// each trial, keyed like launch_perms.
+cudaError_t launch_perms_trials(int32_t *out, int R, int n, uint64_t seed, uint64_t target,
+                                uint64_t stage, uint64_t iter, uint64_t s_first, int n_perm,
+                                int mode, cudaStream_t st);
+
 // Many requests of launch_perms in one launch; request r writes n_perm
 // permutations of [0, n) at out (stride n) for s = s_first .. s_first+n_perm-1,
 // and owns launch CTAs perm_begin .. perm_begin + n_perm - 1.

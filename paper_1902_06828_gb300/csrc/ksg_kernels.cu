@@ -1669,6 +1669,91 @@ cudaError_t launch_perms(int32_t *out, long long stride, int n, uint64_t seed, u
     return cudaGetLastError();
 }
 
+// Surrogates of pooled replications: R trials of n points (point r*n + t).
+// One CTA per surrogate s = s_first + blockIdx.x, state keyed as in
+// fisher_yates_kernel.  mode 0: Fisher-Yates of the R trials, point r*n + t
+// reads sigma[r]*n + t; mode 1: one Fisher-Yates shuffle per trial, trial 0
+// first, all from one continuing generator (R = 1 gives the flat permutation).
+__global__ void fisher_yates_trials_kernel(int32_t *out, int R, int n, uint64_t seed,
+                                           uint64_t target, uint64_t stage, uint64_t iter,
+                                           uint64_t s_first, int mode, int in_smem)
+{
+    extern __shared__ int32_t sbuf[];
+    const uint64_t s = s_first + blockIdx.x;
+    const long long total = (long long)R * n;
+    int32_t *dst = out + (long long)blockIdx.x * total;
+    uint64_t h = sm64_once(seed ^ target);
+    h = sm64_once(h ^ stage);
+    h = sm64_once(h ^ iter);
+    uint64_t st = sm64_once(h ^ s);
+    if (mode == 0) {
+        int32_t *sigma = sbuf;   // [R]
+        for (int r = threadIdx.x; r < R; r += blockDim.x) sigma[r] = r;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int i = R - 1; i >= 1; --i) {
+                const uint64_t x = sm64_next(st);
+                const int j = (int)__umul64hi(x, (uint64_t)(i + 1));
+                const int t = sigma[i];
+                sigma[i] = sigma[j];
+                sigma[j] = t;
+            }
+        __syncthreads();
+        for (long long p = threadIdx.x; p < total; p += blockDim.x) {
+            const int r = (int)(p / n), t = (int)(p - (long long)r * n);
+            dst[p] = sigma[r] * n + t;
+        }
+        return;
+    }
+    int32_t *q = in_smem ? sbuf : dst;
+    for (long long p = threadIdx.x; p < total; p += blockDim.x) q[p] = (int32_t)p;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int r = 0; r < R; ++r) {
+            int32_t *b = q + (long long)r * n;
+            for (int i = n - 1; i >= 1; --i) {
+                const uint64_t x = sm64_next(st);
+                const int j = (int)__umul64hi(x, (uint64_t)(i + 1));
+                const int t = b[i];
+                b[i] = b[j];
+                b[j] = t;
+            }
+        }
+    __syncthreads();
+    if (in_smem)
+        for (long long p = threadIdx.x; p < total; p += blockDim.x) dst[p] = q[p];
+}
+
+cudaError_t launch_perms_trials(int32_t *out, int R, int n, uint64_t seed, uint64_t target,
+                                uint64_t stage, uint64_t iter, uint64_t s_first, int n_perm,
+                                int mode, cudaStream_t st)
+{
+    if (n_perm <= 0) return cudaSuccess;
+    if (R < 1 || n < 1 || (mode != 0 && mode != 1) || (long long)R * n >= (1LL << 31))
+        return cudaErrorInvalidValue;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(
+            reinterpret_cast<const void *>(&fisher_yates_trials_kernel),
+            cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    const size_t whole = (size_t)R * n * sizeof(int32_t);
+    size_t smem;
+    int in_smem = 0;
+    if (mode == 0) {
+        smem = (size_t)R * sizeof(int32_t);
+        if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    } else {
+        in_smem = whole <= 200 * 1024;
+        smem = in_smem ? whole : 0;
+    }
+    fisher_yates_trials_kernel<<<n_perm, 256, smem, st>>>(out, R, n, seed, target, stage, iter,
+                                                          s_first, mode, in_smem);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_perms_multi(const PermJob *jobs, int n_jobs, long long total, int max_n,
                                cudaStream_t st)
 {

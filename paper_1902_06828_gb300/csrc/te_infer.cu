@@ -113,8 +113,15 @@ te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_para
         if (!data || !params || !out) return fail(ctx, TE_EINVAL, "NULL argument");
         if (data->ctx != ctx) return fail(ctx, TE_EINVAL, "data belongs to another context");
         te_infer_params P = *params;
-        const int n_proc = data->n_proc, T = data->T;
+        // pooled replications: candidates over the original processes, every
+        // variable (p, l) read from the pooled row p * (L + 1) + l at lag 0
+        const bool pooled = data->emb_lag >= 0;
+        const int n_proc = pooled ? data->n_proc_orig : data->n_proc, T = data->T;
         const int S = P.n_surr;
+        if (pooled && P.theiler != 0)
+            return fail(ctx, TE_EINVAL, "no Theiler window is defined across pooled trials");
+        if (pooled && (P.surr_mode < 0 || P.surr_mode > 2))
+            return fail(ctx, TE_EINVAL, "surr_mode must be 0, 1 or 2");
         if (P.max_lag_target < 1 || P.max_lag_sources < 1)
             return fail(ctx, TE_EINVAL, "max lags must be >= 1");
         if (P.k < 1 || P.k > TE_MAX_K) return fail(ctx, TE_EINVAL, "k must be in 1..16");
@@ -134,8 +141,26 @@ te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_para
         if (P.fdr && !(P.alpha_fdr > 0.0 && P.alpha_fdr < 1.0))
             return fail(ctx, TE_EINVAL, "alpha_fdr must be in (0, 1)");
         const int t0 = std::max(P.max_lag_target, P.max_lag_sources);
-        if (t0 >= T) return fail(ctx, TE_EINVAL, "max lag must be below T");
-        const int N = T - t0;
+        if (pooled && t0 != data->emb_lag)
+            return fail(ctx, TE_EINVAL, "max(l_target, l_sources) must equal the trials' max_lag");
+        if (!pooled && t0 >= T) return fail(ctx, TE_EINVAL, "max lag must be below T");
+        const int t0_est = pooled ? 0 : t0;   // first point of the estimator's columns
+        const int N = T - t0_est;
+        auto tv = [&](te_var v) {
+            return pooled ? te_var{v.proc * (t0 + 1) + v.lag, 0} : v;
+        };
+        auto tvs = [&](const std::vector<te_var> &vs) {
+            std::vector<te_var> o;
+            for (const te_var &v : vs) o.push_back(tv(v));
+            return o;
+        };
+        // trial surrogates: 0 = shuffle the trial order, 1 = inside trials
+        int trial_mode = 1;
+        if (pooled) {
+            double orders = 1.0;
+            for (int r = 2; r <= data->n_rep; ++r) orders *= r;
+            trial_mode = P.surr_mode == 1 ? 0 : P.surr_mode == 2 ? 1 : (orders >= S ? 0 : 1);
+        }
         if ((long long)N - 1 - 2LL * P.theiler < P.k)
             return fail(ctx, TE_EINVAL, "fewer than k valid neighbours for some point");
         std::vector<int> targets;
@@ -194,29 +219,39 @@ te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_para
                 const int iter = (t.stage == ST_OMNIBUS || t.stage == ST_SEQ) ? 0 : t.it;
                 const size_t n_sets = set_off[r + 1] - set_off[r];
                 for (size_t c = 0; c < n_sets; ++c) {
-                    CK(launch_perms(pr + c * (size_t)S * N, N, N, P.seed, (uint64_t)t.target,
-                                    (uint64_t)t.stage, (uint64_t)iter, 1 + ((uint64_t)c << 32),
-                                    S, ctx->stream),
-                       "permutation launch");
+                    const uint64_t s1 = 1 + ((uint64_t)c << 32);
+                    if (pooled)
+                        CK(launch_perms_trials(pr + c * (size_t)S * N, data->n_rep,
+                                               data->trial_len, P.seed, (uint64_t)t.target,
+                                               (uint64_t)t.stage, (uint64_t)iter, s1, S,
+                                               trial_mode, ctx->stream),
+                           "permutation launch");
+                    else
+                        CK(launch_perms(pr + c * (size_t)S * N, N, N, P.seed, (uint64_t)t.target,
+                                        (uint64_t)t.stage, (uint64_t)iter, s1, S, ctx->stream),
+                           "permutation launch");
                     ctx->stats.launches++;
                 }
-                const te_var ypres{t.target, 0};
+                const te_var ypres = tv(te_var{t.target, 0});
                 // candidate `c0 + c` of the test uses permutation set c0 + c when
                 // every candidate has its own set, set 0 otherwise
                 auto add_group = [&](const std::vector<te_var> &z,
                                      const std::vector<std::vector<te_var>> &xs, size_t c0) {
                     HostGroup g;
                     g.data = data;
-                    g.max_lag = t0;
+                    g.max_lag = t0_est;
                     g.k = P.k;
                     g.theiler = P.theiler;
                     g.y = {ypres};
-                    g.z = z;
+                    g.z = tvs(z);
                     g.dx = (int)xs[0].size();
                     // members surrogate-major, so the members a CTA shares carry
                     // the same permutation; output slots stay candidate-major
                     const int nx = (int)xs.size();
-                    for (const auto &x : xs) g.xvars.insert(g.xvars.end(), x.begin(), x.end());
+                    for (const auto &x : xs) {
+                        const auto xt = tvs(x);
+                        g.xvars.insert(g.xvars.end(), xt.begin(), xt.end());
+                    }
                     for (int s = 0; s <= S; ++s)
                         for (int c = 0; c < nx; ++c) {
                             const size_t set = n_sets > 1 ? c0 + (size_t)c : 0;

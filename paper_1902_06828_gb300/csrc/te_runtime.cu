@@ -797,6 +797,51 @@ te_status te_data_create(te_ctx *ctx, const float *series, int32_t n_proc, int32
     GUARD_END
 }
 
+te_status te_data_create_trials(te_ctx *ctx, const float *series, int32_t n_proc, int32_t n_rep,
+                                int32_t T, int32_t max_lag, int series_on_device, te_data **out)
+{
+    if (!ctx) return TE_EINVAL;
+    GUARD_BEGIN
+    ctx->err.clear();
+    if (!series || !out) return fail(ctx, TE_EINVAL, "series or out is NULL");
+    if (n_proc < 1 || n_rep < 1 || max_lag < 0 || T - max_lag < 2)
+        return fail(ctx, TE_EINVAL, "need n_proc, n_rep >= 1, 0 <= max_lag and T - max_lag >= 2");
+    const long long rows = (long long)n_proc * (max_lag + 1);
+    const long long npool = (long long)n_rep * (T - max_lag);
+    if ((long long)n_proc * n_rep * T >= (1LL << 31) || rows * npool >= (1LL << 31))
+        return fail(ctx, TE_EINVAL, "pooled data must hold fewer than 2^31 values");
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    std::vector<float> raw;
+    const float *src = series;
+    if (series_on_device) {
+        raw.resize((size_t)n_proc * n_rep * T);
+        CK(cudaMemcpy(raw.data(), series, raw.size() * sizeof(float), cudaMemcpyDeviceToHost),
+           "cudaMemcpy");
+        src = raw.data();
+    }
+    // row p * (L + 1) + l, point r * (T - L) + t: process p, trial r, time L + t - l
+    const int L = max_lag, n = T - max_lag;
+    std::vector<float> pooled((size_t)rows * npool);
+    for (int p = 0; p < n_proc; ++p)
+        for (int l = 0; l <= L; ++l) {
+            float *row = pooled.data() + ((size_t)p * (L + 1) + l) * npool;
+            for (int r = 0; r < n_rep; ++r) {
+                const float *tr = src + ((size_t)p * n_rep + r) * T + (L - l);
+                std::copy(tr, tr + n, row + (size_t)r * n);
+            }
+        }
+    te_data *D = nullptr;
+    te_status st = te_data_create(ctx, pooled.data(), (int32_t)rows, (int32_t)npool, 0, &D);
+    if (st) return st;
+    D->n_rep = n_rep;
+    D->trial_len = n;
+    D->emb_lag = L;
+    D->n_proc_orig = n_proc;
+    *out = D;
+    return TE_OK;
+    GUARD_END
+}
+
 void te_data_destroy(te_data *data)
 {
     if (!data) return;

@@ -46,6 +46,10 @@ struct te_data {
     te_ctx *ctx;
     float *d_series;
     int32_t n_proc, T;
+    // pooled replications (te_data_create_trials): the rows are the embedded
+    // columns (p, l), p < n_proc_orig, l <= emb_lag, at row p * (emb_lag + 1) + l,
+    // each holding n_rep trials of trial_len points; emb_lag < 0 for plain data
+    int32_t n_rep = 1, trial_len = 0, emb_lag = -1, n_proc_orig = 0;
 };
 
 struct te_ctx {
