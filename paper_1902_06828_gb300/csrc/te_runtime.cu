@@ -11,6 +11,7 @@
 #include <new>
 #include <string>
 #include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include "te_runtime.h"
@@ -343,17 +344,31 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
     char *obase = (char *)ctx->ws_order.p;
 
     // every surrogate permutation of a sorted group is composed with the
-    // group's order, so kernels index X by position with one load
-    std::map<std::pair<const HostGroup *, const int32_t *>, size_t> cperm_of;
+    // group's order, so kernels index X by position with one load: one
+    // composed copy per distinct (group, permutation), found by hashing
+    struct ComposeEntry {
+        const HostGroup *g;
+        const int32_t *perm;
+        size_t off;
+    };
+    std::vector<ComposeEntry> centries;
+    std::unordered_map<const HostGroup *, std::vector<size_t>> member_cperm;
     size_t cperm_elems = 0;
     for (const HostGroup *g : to_order) {
         const int N = g->data->T - g->max_lag;
-        for (const HostMember &hm : g->members) {
+        std::unordered_map<const int32_t *, size_t> seen;
+        seen.reserve(g->members.size() * 2);
+        std::vector<size_t> &mc = member_cperm[g];
+        mc.assign(g->members.size(), SIZE_MAX);
+        for (size_t i = 0; i < g->members.size(); ++i) {
+            const HostMember &hm = g->members[i];
             if (!hm.perm) continue;
-            auto key = std::make_pair(g, hm.perm);
-            if (cperm_of.count(key)) continue;
-            cperm_of[key] = cperm_elems;
-            cperm_elems += ((size_t)N + 3) & ~(size_t)3;
+            auto ins = seen.emplace(hm.perm, cperm_elems);
+            if (ins.second) {
+                centries.push_back(ComposeEntry{g, hm.perm, cperm_elems});
+                cperm_elems += ((size_t)N + 3) & ~(size_t)3;
+            }
+            mc[i] = ins.first->second;
         }
     }
     if (cperm_elems) {
@@ -504,12 +519,15 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
             gd.member_begin = (int)(mdesc.size() - p.m_off);
             gd.n_members = (int)g->members.size();
             const bool grp_sorted = order_of.count(g) != 0;
-            for (const HostMember &hm : g->members) {
+            const bool grp_fast = fast_set.count(g) != 0;
+            const std::vector<size_t> *mc = grp_sorted ? &member_cperm[g] : nullptr;
+            for (size_t i = 0; i < g->members.size(); ++i) {
+                const HostMember &hm = g->members[i];
                 MemberDesc md;
                 md.perm = hm.perm;
-                if (grp_sorted && hm.perm) md.perm = cbase + cperm_of[std::make_pair(g, hm.perm)];
+                if (grp_sorted && hm.perm) md.perm = cbase + (*mc)[i];
                 md.xsorted = nullptr;
-                if (fast_set.count(g))
+                if (grp_fast)
                     md.xsorted = vbase + vsorted_of[std::make_pair(
                                              g->data, col_off(g, g->xvars[hm.xcol_first]))];
                 md.xcol = xbase + hm.xcol_first;
@@ -563,12 +581,12 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
     }
     std::vector<ComposeJob> cjobs;
     int max_cn = 0;
-    for (auto &kv : cperm_of) {
-        const HostGroup *g = kv.first.first;
+    for (const ComposeEntry &ce : centries) {
+        const HostGroup *g = ce.g;
         ComposeJob J;
         J.sigma = (const int *)(obase + order_of[g].sigma);
-        J.perm = kv.first.second;
-        J.out = cbase + kv.second;
+        J.perm = ce.perm;
+        J.out = cbase + ce.off;
         J.N = g->data->T - g->max_lag;
         max_cn = std::max(max_cn, J.N);
         cjobs.push_back(J);
@@ -975,13 +993,39 @@ te_status cmi_ksg_batch(te_ctx *ctx, const te_cmi_job *jobs, int32_t n_jobs, dou
     // jobs with the same data, point set, k, window, Y and Z share a group
     std::map<std::vector<long long>, int> gid;
     std::vector<HostGroup> groups;
+    // every job's surrogate permutations in one launch
+    std::vector<PermJob> pj;
+    long long perm_total = 0;
+    int max_n = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        const int S = jobs[j].params.n_surr;
+        if (S <= 0) continue;
+        PermJob q{};
+        q.out = perm + job_perm[j];
+        q.n = job_N[j];
+        q.n_perm = S;
+        q.s_first = 1;
+        q.seed = jobs[j].params.seed;
+        q.target = jobs[j].params.stream_tag;
+        q.stage = 0;
+        q.iter = 0;
+        q.perm_begin = perm_total;
+        perm_total += S;
+        max_n = std::max(max_n, job_N[j]);
+        pj.push_back(q);
+    }
+    if (!pj.empty()) {
+        const size_t bytes = pj.size() * sizeof(PermJob);
+        if ((st = ensure_dev(ctx, ctx->ws_stat, bytes + 16))) return st;
+        CK(copy_h2d(ctx, ctx->ws_stat.p, pj.data(), bytes), "cudaMemcpyAsync");
+        CK(launch_perms_multi((const PermJob *)ctx->ws_stat.p, (int)pj.size(), perm_total, max_n,
+                              ctx->stream),
+           "permutation launch");
+        ctx->stats.launches++;
+    }
     for (int j = 0; j < n_jobs; ++j) {
         const te_cmi_job &J = jobs[j];
         const int N = job_N[j], S = J.params.n_surr;
-        CK(launch_perms(perm + job_perm[j], N, N, J.params.seed, J.params.stream_tag, 0, 0, 1, S,
-                        ctx->stream),
-           "permutation launch");
-        if (S > 0) ctx->stats.launches++;
         std::vector<long long> key{(long long)(uintptr_t)J.data, J.params.max_lag, J.params.k,
                                    J.params.theiler, J.dx, J.dy, J.dz};
         for (int d = 0; d < J.dy; ++d) key.push_back(((long long)J.y[d].proc << 32) | J.y[d].lag);
