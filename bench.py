@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "KSG CMI estimates/s incl. surrogates at T=10000"
 UNIT = "estimates/s"
+TRAFFIC_PER_MEMBER_POINT = (147168512.0 + 4281344.0) / (9045 * 3995)
 SM_COUNT = 152
 
 
@@ -430,6 +431,15 @@ def main():
     ops = s1["ksg_ops"] - s0["ksg_ops"]
     achieved = ops / (kernel_ms / 1e3) / 1e12 if kernel_ms > 0 else None
     peak = SM_COUNT * 128 * sm_max * 1e6 / 1e12
+    # DRAM traffic of the KSG kernel per launch: the ncu capture of the same
+    # kernel (T = 4000, step-2 launch of target 0, 9045 members x 3995 points)
+    # read 147.17 MB and wrote 4.28 MB, i.e. 4.19 bytes per member-point (each
+    # member's X row read once); scaled here by the member-points one launch
+    # processes.  Algorithmic bytes: 4 N per member (its X row) + 16 (key).
+    n_pts = args.T - 5
+    mp_per_launch = (n_est / world) * n_pts / max(ksg_launches, 1)   # this rank's launches
+    traffic = TRAFFIC_PER_MEMBER_POINT * mp_per_launch if ksg_launches else None
+    alg_bytes = (4.0 * n_pts + 16.0) * (n_est / world) / max(ksg_launches, 1)
     value = n_est / (ms / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -444,7 +454,10 @@ def main():
                 "steps": e2e_steps},
         "gpu_launches": s1["launches"] - s0["launches"],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "traffic_note": "dram read+write bytes per launch, scaled from the ncu "
+                                     "capture of this kernel at T=4000 by member-points",
+                     "algorithmic_bytes_per_launch": alg_bytes,
                      "kernel": "ksg_lane_kernel", "kernel_ms_per_launch":
                      kernel_ms / max(ksg_launches, 1), "launches": ksg_launches,
                      "peak_note": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived)",
