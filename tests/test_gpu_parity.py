@@ -177,6 +177,29 @@ def test_batch_beyond_grid_limits(te, ctx):
     assert keys[329] == ok
 
 
+@pytest.mark.parametrize("z", [[], [(2, 1), (2, 3)]])
+def test_beyond_the_ordering_limit(te, ctx, z):
+    """N = 19997 points (above the 16384 that one ordering CTA sorts): groups
+    stay in time order; keys and per-point counts equal the oracle's."""
+    rng = np.random.default_rng(19)
+    T = 20000
+    s = rng.normal(size=(3, T))
+    s[2, 1:] += 0.5 * s[1, :-1]
+    s = synth.standardise_jitter(s, 19)
+    data = te.te_data_create(ctx, s)
+    x, y = [(1, 1)], [(2, 0)]
+    cmi, keys = te.cmi_ksg(ctx, data, x, y, z, k=4, max_lag=3, n_surr=2, seed=5, stream_tag=1,
+                           return_keys=True)
+    ok, ik, ip, perms = _oracle_members(s, x, y, z, 4, 0, 3, 2, 5, 1)
+    assert keys == ok
+    assert np.array_equal(cmi, ik) and _close(cmi, ip)
+    g = te.cmi_ksg_debug(ctx, data, x, y, z, member=2, k=4, max_lag=3, n_surr=2, seed=5,
+                         stream_tag=1)
+    o = oksg.cmi_ksg(s, x, y, z, k=4, max_lag=3, perm=perms[1], per_point=True)
+    for c in ("eps", "n_xz", "n_yz", "n_z"):
+        np.testing.assert_array_equal(g[c], o[c])
+
+
 def test_duplicates_and_minimum_size(te, ctx):
     s = np.array([[0, 0, 0, 5, 1, 1], [0, 0, 0, 5, 2, 2]], np.float32)
     data = te.te_data_create(ctx, s)

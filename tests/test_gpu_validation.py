@@ -42,3 +42,13 @@ def test_e2_false_positive_rate_matches_oracle(ctx):
         assert adj.sum() == 0
         rates.append(val.fpr_target(_oracle_adj(series, 0.1, 40, 7 + s)))
     assert rows[0]["fpr_target"] == float(np.mean(rates))
+
+
+def test_empty_network_false_positive_rate_over_50_seeds(ctx):
+    # complete null: 50 empty 10-node VAR networks; the per-target false
+    # positive rate lies in the 0.1-99.9% range of the mean of 50 i.i.d.
+    # Binomial(10, alpha) / 10 (deterministic seeds)
+    rows = val.run_e2(ctx, "var", sizes=(10,), alphas=(0.05,), n_sims=50, T=1000, n_surr=100,
+                      seed=11, out=lambda s: None)
+    lo, hi = val.fpr_expected_range(10, 0.05, 50, q=(0.001, 0.999))
+    assert lo <= rows[0]["fpr_target"] <= hi, rows[0]

@@ -536,3 +536,21 @@ def test_network_with_one_trial_equals_ordinary_network():
     adj2, r2 = onet.infer_network(w["series"][:, None, :], onet.Params(**kw), trials="within")
     assert np.array_equal(adj1, adj2)
     assert [t.trace for t in r1] == [t.trace for t in r2]
+
+
+def test_surrogate_rank_uniform_under_independence():
+    # With X independent of Y and Z, the original and its S surrogates are
+    # exchangeable, so cnt = #{surrogate > original} is uniform on 0..S; over
+    # 200 seeds a chi-square test (19 dof, 99.99th percentile 52.6) holds.
+    S = 19
+    counts = np.zeros(S + 1, int)
+    for seed in range(200):
+        s = synth.independent(3, 260, seed).astype(np.float32)
+        N = 259
+        perms = np.stack([ksg.permutation(seed, 0, 0, 0, q, N) for q in range(1, S + 1)])
+        keys, _, _ = ksg.cmi_ksg_batch(s, [[(0, 1)]] * (S + 1), [(1, 0)], [(2, 1)], perms=perms,
+                                       perm_idx=[-1] + list(range(S)), k=4, max_lag=1)
+        counts[sum(1 for v in keys[1:] if v > keys[0])] += 1
+    exp = 200 / (S + 1)
+    chi2 = float(((counts - exp) ** 2 / exp).sum())
+    assert chi2 < 52.6, (chi2, counts.tolist())
