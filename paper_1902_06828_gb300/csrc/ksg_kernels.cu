@@ -727,14 +727,12 @@ __global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
     // reads read-only data (tbox, s_cqbox) and `bound`, a register snapshot of
     // the CTA's largest per-query bound taken right after a barrier.
     const bool coarse = sorted && jt == 256 && G.tbox != nullptr;
-    auto snapshot = [&]() {
-        float b = 0.f;
-        for (int e = 0; e < LW * LQ; ++e) b = fmaxf(b, (&s_bound[0][0])[e]);
-        return b;
-    };
+    static_assert(LW * LQ == 32, "one bound per lane");
+    auto snapshot = [&]() { return warp_max((&s_bound[0][0])[lane]); };
     auto tile_dead = [&](int t, bool pass1, float bound) {
         if (!coarse) return false;
         float lb = 0.f;
+#pragma unroll 4
         for (int d = pass1 ? 0 : dy; d < dyz; ++d) {
             const float2 b = G.tbox[(size_t)d * G.n_tiles256 + t];
             const float2 q = s_cqbox[d];
@@ -881,6 +879,7 @@ __global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
                     const float *qc = s_q + (warp * LQ + a) * dyz;
                     const int gc = (j0 >> 3) + c;
                     float lb = 0.f;
+#pragma unroll 4
                     for (int d = pass1 ? 0 : dy; d < dyz; ++d) {
                         const float2 b = __ldg(&G.box[(size_t)d * G.n_chunks8 + gc]);
                         const float q = qc[d];
