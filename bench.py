@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "KSG CMI estimates/s incl. surrogates at T=10000"
 UNIT = "estimates/s"
-TRAFFIC_PER_MEMBER_POINT = (147168512.0 + 4281344.0) / (9045 * 3995)
+TRAFFIC_PER_MEMBER_POINT = (146434560.0 + 4099584.0) / (9045 * 3995)
 SM_COUNT = 152
 
 
@@ -433,7 +433,7 @@ def main():
     peak = SM_COUNT * 128 * sm_max * 1e6 / 1e12
     # DRAM traffic of the KSG kernel per launch: the ncu capture of the same
     # kernel (T = 4000, step-2 launch of target 0, 9045 members x 3995 points)
-    # read 147.17 MB and wrote 4.28 MB, i.e. 4.19 bytes per member-point (each
+    # read 146.43 MB and wrote 4.10 MB, i.e. 4.17 bytes per member-point (each
     # member's X row read once); scaled here by the member-points one launch
     # processes.  Algorithmic bytes: 4 N per member (its X row) + 16 (key).
     n_pts = args.T - 5
