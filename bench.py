@@ -283,6 +283,64 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_gauss(args):
+    """Linear-Gaussian estimator path on the 100-node VAR shape (ER p = 0.03,
+    T = 10^4): cmi_gauss calls of one source candidate against the target
+    present given 1..29 conditioning dims, 1000 surrogates each; error of
+    sampled results against the FP64 oracle beside the returned bounds."""
+    import torch
+    import paper_1902_06828_gb300 as te
+    import synth
+    from oracle import gauss as ogauss
+    from oracle import ksg as oksg
+    x, _, _ = synth.var_er(n=100, p=0.03, T=args.T, seed=1)
+    series = synth.standardise_jitter(x, 1)
+    ctx = te.Context(0)
+    data = te.te_data_create(ctx, series)
+    S, L = 1000, 5
+    calls = []
+    for a, dz in enumerate(range(1, 31, 2)):   # joint dims 3..31 (the ABI allows 32)
+        z = [(0, l) for l in range(1, 6)][:dz] + [(1 + q, 1 + (q % 5)) for q in range(max(0, dz - 5))]
+        calls.append(dict(x=[(50 + a, 1 + a % 5)], y=[(0, 0)], z=z[:dz], tag=a))
+    for c in calls[:2]:
+        te.cmi_gauss(ctx, data, c["x"], c["y"], c["z"], max_lag=L, n_surr=S, seed=2,
+                     stream_tag=c["tag"])
+    torch.cuda.synchronize()
+    lat = []
+    res = []
+    t0 = time.perf_counter()
+    for c in calls:
+        t1 = time.perf_counter()
+        res.append(te.cmi_gauss(ctx, data, c["x"], c["y"], c["z"], max_lag=L, n_surr=S, seed=2,
+                                stream_tag=c["tag"]))
+        lat.append((time.perf_counter() - t1) * 1e3)
+    span = time.perf_counter() - t0
+    est = len(calls) * (S + 1)
+    # FP64 oracle on sampled surrogates of the first and last call
+    N = series.shape[1] - L
+    errs, bounds = [], []
+    for ci in (0, len(calls) - 1):
+        c = calls[ci]
+        idx = [0, 1, 500, 1000]
+        perms = np.stack([oksg.permutation(2, c["tag"], 0, 0, s, N) for s in idx[1:]])
+        want = ogauss.cmi_gauss(series, c["x"], c["y"], c["z"], max_lag=L, perms=perms)
+        got = res[ci][0][idx]
+        errs += list(np.abs(got - want))
+        bounds += list(res[ci][1][idx])
+    line = {"metric": "linear-Gaussian CMI estimates/s incl. surrogates at T=%d" % args.T,
+            "value": est / span, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f64 (tf32-split contraction)", "data": "synthetic",
+            "config": {"workload": "100-node VAR (ER p=0.03, T=%d), x = 1 source lag, y = target "
+                                   "present, z = 1..29 dims, 1000 surrogates per call" % args.T,
+                       "calls": len(calls)},
+            "p50_ms_per_call": float(np.percentile(lat, 50)),
+            "p99_ms_per_call": float(np.percentile(lat, 99)),
+            "max_abs_err_vs_fp64_oracle": float(max(errs)),
+            "max_err_bound_returned": float(max(bounds)),
+            "errors_within_bounds": bool(all(e <= b for e, b in zip(errs, bounds)))}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -332,6 +390,8 @@ def main():
     ap.add_argument("--serve", action="store_true",
                     help="run the serving workload instead of the network benchmark")
     ap.add_argument("--serve-requests", type=int, default=80)
+    ap.add_argument("--gauss", action="store_true",
+                    help="linear-Gaussian estimator path (cmi_gauss) instead of the KSG network")
     ap.add_argument("--plain-calls", type=int, default=30,
                     help="one-call-per-estimate calls timed for the plain-path comparison")
     args = ap.parse_args()
@@ -339,6 +399,8 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
+    if args.gauss:
+        return run_gauss(args)
     if args.serve:
         run_serve(args)
         return

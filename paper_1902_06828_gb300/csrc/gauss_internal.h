@@ -25,7 +25,14 @@ struct GaussArgs {
                             // [1] 1: a tensor-core wait timed out
     double *cross;          // [S + 1][dx][dw] cross-covariance of permuted X with W
     double *out, *err;      // [S + 1] estimates and error bounds
+    // the contraction is split along the points: split p sums chunks
+    // [p * chunks_per_split, ...) into cross_part[p][S + 1][dx][dw]
+    int splits, chunks_per_split;
+    double *cross_part;
 };
+// splits of the points for (S + 1) * dx rows of N points (fills about two
+// waves of CTAs; every split keeps at least one accumulation group)
+int gauss_cross_splits(int rows, int N);
 
 cudaError_t gauss_launch_stats(const GaussArgs &A, cudaStream_t st);
 cudaError_t gauss_launch_cross_tc(const GaussArgs &A, cudaStream_t st);

@@ -287,6 +287,7 @@ __global__ void __launch_bounds__(128, 1) gauss_cross_tc_kernel(GaussArgs A)
     const int tid = threadIdx.x, warp = tid >> 5;
     const int rows = (A.S + 1) * A.dx;
     const int m = blockIdx.x * kGaussTileM + tid;   // this thread's row
+    const int split = blockIdx.y;
     const bool mvalid = m < rows;
     const int ms = mvalid ? m / A.dx : 0, mi = mvalid ? m % A.dx : 0;
     const int32_t *perm = (mvalid && ms > 0) ? A.perms + (size_t)(ms - 1) * A.N : nullptr;
@@ -318,10 +319,12 @@ __global__ void __launch_bounds__(128, 1) gauss_cross_tc_kernel(GaussArgs A)
 #pragma unroll
     for (int a = 0; a < kGaussTileN; ++a) acc[a] = 0.0;
     uint32_t phase = 0;
-    const int nchunks = (A.N + kGaussKC - 1) / kGaussKC;
+    const int nchunks_all = (A.N + kGaussKC - 1) / kGaussKC;
+    const int ch0 = split * A.chunks_per_split;
+    const int ch1 = min(nchunks_all, ch0 + A.chunks_per_split);
     bool failed = false;
 
-    for (int ch = 0; ch < nchunks && !failed; ++ch) {
+    for (int ch = ch0; ch < ch1 && !failed; ++ch) {
         const int k0 = ch * kGaussKC;
         // stage A: this thread's row, 32 points
         {
@@ -366,7 +369,7 @@ __global__ void __launch_bounds__(128, 1) gauss_cross_tc_kernel(GaussArgs A)
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const bool first = (ch % kGaussGroup) == 0;
+            const bool first = ((ch - ch0) % kGaussGroup) == 0;
 #pragma unroll
             for (int q = 0; q < kGaussKC / 8; ++q) {   // K = 8 TF32 per MMA
                 const uint32_t ko = q * 256;            // two core matrices along K
@@ -396,7 +399,7 @@ __global__ void __launch_bounds__(128, 1) gauss_cross_tc_kernel(GaussArgs A)
         }
         phase ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const bool group_end = (ch % kGaussGroup) == kGaussGroup - 1 || ch == nchunks - 1;
+        const bool group_end = ((ch - ch0) % kGaussGroup) == kGaussGroup - 1 || ch == ch1 - 1;
         if (group_end) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
@@ -408,10 +411,10 @@ __global__ void __launch_bounds__(128, 1) gauss_cross_tc_kernel(GaussArgs A)
     }
     if (failed && tid == 0) atomicExch(A.status + 1, 1);
     if (!failed && mvalid) {
-        const double inv = 1.0 / (double)(A.N - 1);
+        double *part = A.cross_part + ((size_t)split * rows + m) * A.dw;
 #pragma unroll
         for (int n = 0; n < kGaussTileN; ++n)
-            if (n < A.dw) A.cross[(size_t)m * A.dw + n] = acc[n] * inv;
+            if (n < A.dw) part[n] = acc[n];
     }
     __syncthreads();
     if (warp == 0)
@@ -419,7 +422,26 @@ __global__ void __launch_bounds__(128, 1) gauss_cross_tc_kernel(GaussArgs A)
                      "r"((uint32_t)kGaussTileN));
 }
 
+// cross = (sum of the splits' partial sums, in split order) / (N - 1)
+__global__ void gauss_cross_reduce_kernel(GaussArgs A)
+{
+    const long long total = (long long)(A.S + 1) * A.dx * A.dw;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    double s = 0.0;
+    for (int p = 0; p < A.splits; ++p) s += A.cross_part[(size_t)p * total + e];
+    A.cross[e] = s * (1.0 / (double)(A.N - 1));
+}
+
 }  // namespace
+
+int gauss_cross_splits(int rows, int N)
+{
+    const int tiles = (rows + kGaussTileM - 1) / kGaussTileM;
+    const int groups = (N + kGaussKC * kGaussGroup - 1) / (kGaussKC * kGaussGroup);
+    int splits = (2 * 152 + tiles - 1) / tiles;
+    return splits < 1 ? 1 : (splits > groups ? groups : splits);
+}
 
 cudaError_t gauss_launch_stats(const GaussArgs &A, cudaStream_t st)
 {
@@ -436,7 +458,13 @@ cudaError_t gauss_launch_stats(const GaussArgs &A, cudaStream_t st)
 cudaError_t gauss_launch_cross_tc(const GaussArgs &A, cudaStream_t st)
 {
     const int rows = (A.S + 1) * A.dx;
-    gauss_cross_tc_kernel<<<(rows + kGaussTileM - 1) / kGaussTileM, 128, 0, st>>>(A);
+    if (A.splits < 1 || A.splits > 65535) return cudaErrorInvalidValue;
+    gauss_cross_tc_kernel<<<dim3((rows + kGaussTileM - 1) / kGaussTileM, A.splits), 128, 0, st>>>(
+        A);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long total = (long long)rows * A.dw;
+    gauss_cross_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(A);
     return cudaGetLastError();
 }
 

@@ -29,8 +29,10 @@ extern "C" te_status cmi_gauss(te_ctx *ctx, const te_data *data, const te_var *x
         if (N <= d + 1) return fail(ctx, TE_EINVAL, "need more points than variables + 1");
         CK(cudaSetDevice(ctx->device), "cudaSetDevice");
         // workspace layout (doubles first, then ints)
+        const int splits = gauss_cross_splits((S + 1) * dx, N);
+        const int nchunks = (N + 31) / 32;
         const size_t nd = (size_t)d + (size_t)d * d + 2 * (size_t)dw * dw + 2 + kGaussMaxDims +
-                          (size_t)(S + 1) * dx * dw + 2 * (size_t)(S + 1);
+                          (size_t)(S + 1) * dx * dw * (1 + (size_t)splits) + 2 * (size_t)(S + 1);
         const size_t bytes = nd * 8 + (size_t)(d + 8) * 4;
         if ((st = ensure_dev(ctx, ctx->ws_gauss, bytes))) return st;
         if ((st = ensure_dev(ctx, ctx->ws_perm, (size_t)std::max(S, 1) * N * 4))) return st;
@@ -53,7 +55,11 @@ extern "C" te_status cmi_gauss(te_ctx *ctx, const te_data *data, const te_var *x
         A.cross = A.scratch + kGaussMaxDims;
         A.out = A.cross + (size_t)(S + 1) * dx * dw;
         A.err = A.out + (S + 1);
-        int *ip = (int *)(A.err + (S + 1));
+        A.cross_part = A.err + (S + 1);
+        A.splits = splits;
+        A.chunks_per_split = (nchunks + splits - 1) / splits;
+        A.splits = (nchunks + A.chunks_per_split - 1) / A.chunks_per_split;
+        int *ip = (int *)(A.cross_part + (size_t)splits * (S + 1) * dx * dw);
         A.status = ip;
         int *cols_dev = ip + 2;
         A.cols = cols_dev;
@@ -70,7 +76,7 @@ extern "C" te_status cmi_gauss(te_ctx *ctx, const te_data *data, const te_var *x
         CK(gauss_launch_cross_tc(A, ctx->stream), "tensor-core cross-covariance launch");
         const double gamma = gauss_tc_gamma();
         CK(gauss_launch_schur(A, gamma, ctx->stream), "Schur launch");
-        ctx->stats.launches += 6;
+        ctx->stats.launches += 7;
         std::vector<double> res(2 * (size_t)(S + 1));
         int status[2] = {0, 0};
         CK(copy_d2h(ctx, res.data(), A.out, res.size() * 8), "cudaMemcpyAsync");
