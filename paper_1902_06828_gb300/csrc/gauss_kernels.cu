@@ -105,24 +105,83 @@ __device__ double inv_frob2(const double *L, int n, int ld, double *col)
     return s;
 }
 
-// Factor S_ZZ and S_WW (single thread).  W = the Y then Z columns; Z is the
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// In-place FP64 Cholesky of an n x n SPD matrix (n <= 32, row-major, lower
+// factor) by one warp: the pivot's sum is a warp reduction, the column below
+// it one row per lane.  False (in every lane) if a pivot is not positive.
+__device__ bool chol_warp(double *a, int n, int ld)
+{
+    const int lane = threadIdx.x & 31;
+    for (int j = 0; j < n; ++j) {
+        const double v = lane < j ? a[j * ld + lane] : 0.0;
+        const double s = a[j * ld + j] - warp_sum_d(v * v);
+        if (!(s > 0.0)) return false;
+        const double l = sqrt(s);
+        const int i = j + 1 + lane;
+        double t = 0.0;
+        if (i < n) {
+            t = a[i * ld + j];
+            for (int k = 0; k < j; ++k) t -= a[i * ld + k] * a[j * ld + k];
+        }
+        __syncwarp();
+        if (i < n) a[i * ld + j] = t / l;
+        if (lane == 0) a[j * ld + j] = l;
+        __syncwarp();
+    }
+    return true;
+}
+
+// ||L^-1||_F^2 for lower-triangular L (n <= 32) by one warp: lane c solves
+// L x = e_c by forward substitution (x kept in col[c][*], shared memory)
+__device__ double inv_frob2_warp(const double *L, int n, int ld, double (*col)[33])
+{
+    const int c = threadIdx.x & 31;
+    double s = 0.0;
+    if (c < n) {
+        for (int i = 0; i < n; ++i) {
+            double t = (i == c) ? 1.0 : 0.0;
+            for (int k = c; k < i; ++k) t -= L[i * ld + k] * col[c][k];
+            const double x = i < c ? 0.0 : t / L[i * ld + i];
+            col[c][i] = x;
+            s += x * x;
+        }
+    }
+    return warp_sum_d(s);
+}
+
+// Factor S_ZZ and S_WW (one warp).  W = the Y then Z columns; Z is the
 // trailing block of W.  Writes L_W, L_Z (lower, row-major, ld = dw) and
 // ||L^-1||_F^2 of each; status[0] = 1 if a block is not positive definite.
 __global__ void gauss_factor_kernel(GaussArgs A)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double col[32][33];
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
     const int dx = A.dx, dw = A.dw, dy = A.dy, dz = dw - dy, d = A.d;
-    for (int r = 0; r < dw; ++r)
-        for (int c = 0; c < dw; ++c) {
-            A.LW[r * dw + c] = c <= r ? A.cov[(dx + r) * d + dx + c] : 0.0;
-            if (r < dz && c < dz) A.LZ[r * dw + c] = c <= r ? A.cov[(dx + dy + r) * d + dx + dy + c] : 0.0;
-        }
-    bool ok = chol(A.LW, dw, dw);
-    if (dz > 0) ok = ok && chol(A.LZ, dz, dw);
-    A.status[0] = ok ? 0 : 1;
+    for (int e = lane; e < dw * dw; e += 32) {
+        const int r = e / dw, c = e % dw;
+        A.LW[r * dw + c] = c <= r ? A.cov[(dx + r) * d + dx + c] : 0.0;
+        if (r < dz && c < dz) A.LZ[r * dw + c] = c <= r ? A.cov[(dx + dy + r) * d + dx + dy + c] : 0.0;
+    }
+    __syncwarp();
+    bool ok = chol_warp(A.LW, dw, dw);
+    if (dz > 0) ok = ok && chol_warp(A.LZ, dz, dw);
+    if (lane == 0) A.status[0] = ok ? 0 : 1;
     if (!ok) return;
-    A.norms[0] = inv_frob2(A.LW, dw, dw, A.scratch);
-    A.norms[1] = dz > 0 ? inv_frob2(A.LZ, dz, dw, A.scratch) : 0.0;
+    __syncwarp();
+    const double nw = inv_frob2_warp(A.LW, dw, dw, col);
+    __syncwarp();
+    const double nz = dz > 0 ? inv_frob2_warp(A.LZ, dz, dw, col) : 0.0;
+    if (lane == 0) {
+        A.norms[0] = nw;
+        A.norms[1] = nz;
+    }
 }
 
 // Per surrogate (one thread): Schur complements given Z and given W, their

@@ -1196,20 +1196,31 @@ __device__ __forceinline__ uint64_t sm64_next(uint64_t &s)
 
 __device__ __forceinline__ uint64_t sm64_once(uint64_t x) { return sm64_next(x); }
 
-__global__ void fisher_yates_kernel(int32_t *out, long long stride, int n, uint64_t seed,
-                                    uint64_t target, uint64_t stage, uint64_t iter,
-                                    uint64_t s_first, int in_smem)
+// Fisher-Yates shuffle of p[0, n) in place (positions n-1 down to 1, j drawn
+// as floor(r (i + 1) / 2^64)) with the SplitMix64 generator whose state starts
+// at st.  The k-th output of that generator is mix(st + (k + 1) gamma), so with
+// jb (n ints of shared memory) every thread of the CTA computes draws first
+// and one thread then runs the swaps; without it one thread does both.  The
+// permutation is the same either way.  Called by the whole CTA.
+__device__ void fy_shuffle(int32_t *p, int n, uint64_t st, int32_t *jb)
 {
-    extern __shared__ int32_t sperm[];
-    const uint64_t s = s_first + blockIdx.x;
-    int32_t *p = in_smem ? sperm : out + (long long)blockIdx.x * stride;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = i;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint64_t h = sm64_once(seed ^ target);
-        h = sm64_once(h ^ stage);
-        h = sm64_once(h ^ iter);
-        uint64_t st = sm64_once(h ^ s);
+    if (jb) {
+        for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
+            uint64_t z = st + (uint64_t)(n - i) * 0x9E3779B97F4A7C15ull;   // draw k = n-1-i
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            jb[i] = (int)__umul64hi(z, (uint64_t)(i + 1));
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int i = n - 1; i >= 1; --i) {
+                const int j = jb[i];
+                const int32_t t = p[i];
+                p[i] = p[j];
+                p[j] = t;
+            }
+    } else if (threadIdx.x == 0) {
         for (int i = n - 1; i >= 1; --i) {
             const uint64_t r = sm64_next(st);
             const int j = (int)__umul64hi(r, (uint64_t)(i + 1));
@@ -1219,6 +1230,25 @@ __global__ void fisher_yates_kernel(int32_t *out, long long stride, int n, uint6
         }
     }
     __syncthreads();
+}
+
+// in_smem: bit 0 = the permutation is built in shared memory, bit 1 = the
+// draws are computed in parallel into shared memory after it
+__global__ void fisher_yates_kernel(int32_t *out, long long stride, int n, uint64_t seed,
+                                    uint64_t target, uint64_t stage, uint64_t iter,
+                                    uint64_t s_first, int in_smem)
+{
+    extern __shared__ int32_t sperm[];
+    const uint64_t s = s_first + blockIdx.x;
+    int32_t *p = (in_smem & 1) ? sperm : out + (long long)blockIdx.x * stride;
+    int32_t *jb = (in_smem & 2) ? sperm + ((in_smem & 1) ? n : 0) : nullptr;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = i;
+    __syncthreads();
+    uint64_t h = sm64_once(seed ^ target);
+    h = sm64_once(h ^ stage);
+    h = sm64_once(h ^ iter);
+    fy_shuffle(p, n, sm64_once(h ^ s), jb);
+    in_smem &= 1;
     if (in_smem)
         for (int i = threadIdx.x; i < n; i += blockDim.x)
             out[(long long)blockIdx.x * stride + i] = sperm[i];
@@ -1372,7 +1402,7 @@ __global__ void compose_kernel(const ComposeJob *jobs)
 
 // Many permutation requests in one launch: CTA g is permutation g of the
 // concatenated request list (binary search over the requests' first index).
-__global__ void fisher_yates_multi_kernel(const PermJob *jobs, int n_jobs, int smem_n)
+__global__ void fisher_yates_multi_kernel(const PermJob *jobs, int n_jobs, int smem_n, int jb_ok)
 {
     extern __shared__ int32_t sperm[];
     const long long g = blockIdx.x;
@@ -1388,22 +1418,14 @@ __global__ void fisher_yates_multi_kernel(const PermJob *jobs, int n_jobs, int s
     const bool in_smem = n <= smem_n;
     int32_t *dst = J.out + (long long)r * n;
     int32_t *p = in_smem ? sperm : dst;
+    // smem_n >= 0 holds the permutation; a second smem_n ints hold the draws
+    int32_t *jb = (in_smem && jb_ok) ? sperm + smem_n : nullptr;
     for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = i;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        uint64_t h = sm64_once(J.seed ^ J.target);
-        h = sm64_once(h ^ J.stage);
-        h = sm64_once(h ^ J.iter);
-        uint64_t st = sm64_once(h ^ (uint64_t)(J.s_first + r));
-        for (int i = n - 1; i >= 1; --i) {
-            const uint64_t rr = sm64_next(st);
-            const int j = (int)__umul64hi(rr, (uint64_t)(i + 1));
-            const int32_t t = p[i];
-            p[i] = p[j];
-            p[j] = t;
-        }
-    }
-    __syncthreads();
+    uint64_t h = sm64_once(J.seed ^ J.target);
+    h = sm64_once(h ^ J.stage);
+    h = sm64_once(h ^ J.iter);
+    fy_shuffle(p, n, sm64_once(h ^ (uint64_t)(J.s_first + r)), jb);
     if (in_smem)
         for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = sperm[i];
 }
@@ -1663,8 +1685,19 @@ cudaError_t launch_perms(int32_t *out, long long stride, int n, uint64_t seed, u
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
-    fisher_yates_kernel<<<n_perm, 256, in_smem ? smem : 0, st>>>(out, stride, n, seed, target,
-                                                                stage, iter, s_first, in_smem);
+    // permutation and draws in shared memory when both fit, else the
+    // permutation alone, else neither
+    int mode = 0;
+    size_t bytes = 0;
+    if (2 * smem <= 200 * 1024) {
+        mode = 3;
+        bytes = 2 * smem;
+    } else if (in_smem) {
+        mode = 1;
+        bytes = smem;
+    }
+    fisher_yates_kernel<<<n_perm, 256, bytes, st>>>(out, stride, n, seed, target, stage, iter,
+                                                    s_first, mode);
     return cudaGetLastError();
 }
 
@@ -1767,8 +1800,9 @@ cudaError_t launch_perms_multi(const PermJob *jobs, int n_jobs, long long total,
         attr_done = true;
     }
     const int smem_n = max_n * 4 <= 200 * 1024 ? max_n : 0;
-    fisher_yates_multi_kernel<<<(unsigned)total, 256, (size_t)smem_n * 4, st>>>(jobs, n_jobs,
-                                                                               smem_n);
+    const int jb_ok = smem_n > 0 && (size_t)max_n * 8 <= 200 * 1024;
+    fisher_yates_multi_kernel<<<(unsigned)total, 256, (size_t)smem_n * (jb_ok ? 8 : 4), st>>>(
+        jobs, n_jobs, smem_n, jb_ok);
     return cudaGetLastError();
 }
 
