@@ -1511,15 +1511,9 @@ const void *select_kernel(const KsgVariant &v, bool dx1)
         if (v.kt == 4 && v.tma) return reinterpret_cast<const void *>(&ksg_lane_kernel<4, 2, true>);
         return nullptr;
     }
-    if (dx1) {
-        if (v.kt == 4) {
-            if (v.m == 4) return kptr<4, 4, true>();
-            if (v.m == 8) return kptr<8, 4, true>();
-            if (v.m == 16) return kptr<16, 4, true>();
-        } else if (v.kt == 0 && v.m == 2) {
-            return kptr<2, 0, true>();
-        }
-    } else {
+    // single-variable X always runs a member-lane kernel; the fused kernel
+    // serves multi-variable X (the omnibus test's block)
+    if (!dx1) {
         if (v.kt == 4) {
             if (v.m == 2) return kptr<2, 4, false>();
             if (v.m == 4) return kptr<4, 4, false>();
@@ -1534,7 +1528,7 @@ const void *select_kernel(const KsgVariant &v, bool dx1)
 
 cudaError_t ksg_prepare_attributes()
 {
-    const KsgVariant vs[] = {{4, 4, QT},  {8, 4, QT},  {16, 4, QT}, {2, 0, QT},
+    const KsgVariant vs[] = {{4, 4, QT},  {2, 0, QT},
                              {2, 4, QT},  {32, 4, LW * 32}, {32, 0, LW * 32},
                              {32, 4, LW * 32, true}, {32, 0, LW * 32, true},
                              {64, 4, LW * 32, true}};
