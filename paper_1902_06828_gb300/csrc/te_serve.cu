@@ -60,11 +60,11 @@ struct Slot {
 
 // device bytes of one job: permutations and their composed copies (8 S N),
 // the X-value rows of the TMA-staged kernel (4 (S + 1) N, rows padded to a
-// multiple of 4 points), the order and sorted Y/Z columns, the chunk boxes,
+// multiple of 8 points), the order and sorted Y/Z columns, the chunk boxes,
 // accumulators, keys and descriptors
 size_t footprint(int N, int S, int dyz)
 {
-    const size_t pitch = (size_t)std::max(32, (N + 3) & ~3);
+    const size_t pitch = (size_t)std::max(32, (N + 7) & ~7);
     return (size_t)S * N * 8 + (size_t)(S + 1) * pitch * 4 + (size_t)N * (4 + 4 * (size_t)dyz) +
            8 * (size_t)dyz * (N / 8 + 1) + 64 * (size_t)(S + 1) + 4096;
 }
