@@ -1232,14 +1232,48 @@ __device__ void fy_shuffle(int32_t *p, int n, uint64_t st, int32_t *jb)
     __syncthreads();
 }
 
+// The same shuffle for n <= 65535 with the permutation and the draws as
+// 16-bit values in shared memory (4 bytes per point: more CTAs per SM), the
+// result widened into out.  Called by the whole CTA.
+__device__ void fy_shuffle16(uint16_t *p, uint16_t *jb, int n, uint64_t st, int32_t *out)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = (uint16_t)i;
+    for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
+        uint64_t z = st + (uint64_t)(n - i) * 0x9E3779B97F4A7C15ull;   // draw k = n-1-i
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        jb[i] = (uint16_t)__umul64hi(z, (uint64_t)(i + 1));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int i = n - 1; i >= 1; --i) {
+            const int j = jb[i];
+            const uint16_t t = p[i];
+            p[i] = p[j];
+            p[j] = t;
+        }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = (int32_t)p[i];
+}
+
 // in_smem: bit 0 = the permutation is built in shared memory, bit 1 = the
-// draws are computed in parallel into shared memory after it
+// draws are computed in parallel into shared memory after it, 4 = both as
+// 16-bit values (n <= 65535)
 __global__ void fisher_yates_kernel(int32_t *out, long long stride, int n, uint64_t seed,
                                     uint64_t target, uint64_t stage, uint64_t iter,
                                     uint64_t s_first, int in_smem)
 {
     extern __shared__ int32_t sperm[];
     const uint64_t s = s_first + blockIdx.x;
+    if (in_smem == 4) {
+        uint64_t h = sm64_once(seed ^ target);
+        h = sm64_once(h ^ stage);
+        h = sm64_once(h ^ iter);
+        uint16_t *p16 = reinterpret_cast<uint16_t *>(sperm);
+        fy_shuffle16(p16, p16 + n, n, sm64_once(h ^ s), out + (long long)blockIdx.x * stride);
+        return;
+    }
     int32_t *p = (in_smem & 1) ? sperm : out + (long long)blockIdx.x * stride;
     int32_t *jb = (in_smem & 2) ? sperm + ((in_smem & 1) ? n : 0) : nullptr;
     for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = i;
@@ -1417,6 +1451,14 @@ __global__ void fisher_yates_multi_kernel(const PermJob *jobs, int n_jobs, int s
     const int n = J.n;
     const bool in_smem = n <= smem_n;
     int32_t *dst = J.out + (long long)r * n;
+    uint64_t h0 = sm64_once(J.seed ^ J.target);
+    h0 = sm64_once(h0 ^ J.stage);
+    h0 = sm64_once(h0 ^ J.iter);
+    if (in_smem && n <= 65535) {
+        uint16_t *p16 = reinterpret_cast<uint16_t *>(sperm);
+        fy_shuffle16(p16, p16 + n, n, sm64_once(h0 ^ (uint64_t)(J.s_first + r)), dst);
+        return;
+    }
     int32_t *p = in_smem ? sperm : dst;
     // smem_n >= 0 holds the permutation; a second smem_n ints hold the draws
     int32_t *jb = (in_smem && jb_ok) ? sperm + smem_n : nullptr;
@@ -1683,7 +1725,10 @@ cudaError_t launch_perms(int32_t *out, long long stride, int n, uint64_t seed, u
     // permutation alone, else neither
     int mode = 0;
     size_t bytes = 0;
-    if (2 * smem <= 200 * 1024) {
+    if (n <= 65535 && smem <= 200 * 1024) {
+        mode = 4;
+        bytes = smem;   // 2 + 2 bytes per point
+    } else if (2 * smem <= 200 * 1024) {
         mode = 3;
         bytes = 2 * smem;
     } else if (in_smem) {
@@ -1794,7 +1839,9 @@ cudaError_t launch_perms_multi(const PermJob *jobs, int n_jobs, long long total,
         attr_done = true;
     }
     const int smem_n = max_n * 4 <= 200 * 1024 ? max_n : 0;
-    const int jb_ok = smem_n > 0 && (size_t)max_n * 8 <= 200 * 1024;
+    // n <= 65535 shuffles in 16 bits (4 bytes per point); larger ones keep
+    // their draws beside the permutation when that fits
+    const int jb_ok = smem_n > 0 && max_n > 65535 && (size_t)max_n * 8 <= 200 * 1024;
     fisher_yates_multi_kernel<<<(unsigned)total, 256, (size_t)smem_n * (jb_ok ? 8 : 4), st>>>(
         jobs, n_jobs, smem_n, jb_ok);
     return cudaGetLastError();
