@@ -1196,6 +1196,50 @@ __device__ __forceinline__ uint64_t sm64_next(uint64_t &s)
 
 __device__ __forceinline__ uint64_t sm64_once(uint64_t x) { return sm64_next(x); }
 
+// Apply the swaps (i, jb[i]) for i = n-1 down to 1 to p, in that order, by
+// warp 0 of the CTA.  Steps go in batches of 32 consecutive positions: when
+// every draw of a batch lies below the batch's lowest position and no two
+// draws are equal, the batch's swaps touch disjoint positions and commute, so
+// the 32 lanes apply them at once; otherwise lane 0 applies the batch in
+// order.  The result equals the sequential loop exactly.
+template <typename P, typename J>
+__device__ void fy_apply(P *p, const J *jb, int n)
+{
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    for (int hi = n - 1; hi >= 1;) {
+        const int lo = hi - 31 > 1 ? hi - 31 : 1;
+        const int i = hi - lane;
+        const bool valid = i >= lo;
+        const int j = valid ? (int)jb[i] : -1 - lane;   // invalid lanes: distinct dummies
+        const unsigned same = __match_any_sync(0xffffffffu, j);
+        const bool ok = !valid || (j < lo && __popc(same) == 1);
+        if (__all_sync(0xffffffffu, ok)) {
+            P a = 0, b = 0;
+            if (valid) {
+                a = p[i];
+                b = p[j];
+            }
+            __syncwarp();
+            if (valid) {
+                p[i] = b;
+                p[j] = a;
+            }
+            __syncwarp();
+        } else {
+            if (lane == 0)
+                for (int ii = hi; ii >= lo; --ii) {
+                    const int jj = (int)jb[ii];
+                    const P t = p[ii];
+                    p[ii] = p[jj];
+                    p[jj] = t;
+                }
+            __syncwarp();
+        }
+        hi = lo - 1;
+    }
+}
+
 // Fisher-Yates shuffle of p[0, n) in place (positions n-1 down to 1, j drawn
 // as floor(r (i + 1) / 2^64)) with the SplitMix64 generator whose state starts
 // at st.  The k-th output of that generator is mix(st + (k + 1) gamma), so with
@@ -1213,13 +1257,7 @@ __device__ void fy_shuffle(int32_t *p, int n, uint64_t st, int32_t *jb)
             jb[i] = (int)__umul64hi(z, (uint64_t)(i + 1));
         }
         __syncthreads();
-        if (threadIdx.x == 0)
-            for (int i = n - 1; i >= 1; --i) {
-                const int j = jb[i];
-                const int32_t t = p[i];
-                p[i] = p[j];
-                p[j] = t;
-            }
+        fy_apply(p, jb, n);
     } else if (threadIdx.x == 0) {
         for (int i = n - 1; i >= 1; --i) {
             const uint64_t r = sm64_next(st);
@@ -1246,13 +1284,7 @@ __device__ void fy_shuffle16(uint16_t *p, uint16_t *jb, int n, uint64_t st, int3
         jb[i] = (uint16_t)__umul64hi(z, (uint64_t)(i + 1));
     }
     __syncthreads();
-    if (threadIdx.x == 0)
-        for (int i = n - 1; i >= 1; --i) {
-            const int j = jb[i];
-            const uint16_t t = p[i];
-            p[i] = p[j];
-            p[j] = t;
-        }
+    fy_apply(p, jb, n);
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = (int32_t)p[i];
 }
