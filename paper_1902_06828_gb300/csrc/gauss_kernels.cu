@@ -385,24 +385,34 @@ __global__ void __launch_bounds__(128, 1) gauss_cross_tc_kernel(GaussArgs A)
 
     for (int ch = ch0; ch < ch1 && !failed; ++ch) {
         const int k0 = ch * kGaussKC;
-        // stage A: this thread's row, 32 points
+        // stage A: this thread's row, 32 points, 16 at a time: all permutation
+        // entries, then all values, are loaded before any is used
         {
             unsigned char *hb = reinterpret_cast<unsigned char *>(sA_hi);
             unsigned char *lb = reinterpret_cast<unsigned char *>(sA_lo);
-#pragma unroll 4
-            for (int k = 0; k < kGaussKC; ++k) {
-                const int t = k0 + k;
-                float hi = 0.f, lo = 0.f;
-                if (mvalid && t < A.N) {
-                    const int tx = perm ? perm[t] : t;
-                    const double v = (double)cx[tx] - mx;
-                    const uint32_t h = to_tf32((float)v);
-                    hi = __uint_as_float(h);
-                    lo = __uint_as_float(to_tf32((float)(v - (double)hi)));
+#pragma unroll
+            for (int h16 = 0; h16 < kGaussKC; h16 += 16) {
+                int tx[16];
+                float xv[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int t = k0 + h16 + k;
+                    tx[k] = (mvalid && t < A.N) ? (perm ? perm[t] : t) : -1;
                 }
-                const uint32_t off = cm_offset(tid, k);
-                *reinterpret_cast<float *>(hb + off) = hi;
-                *reinterpret_cast<float *>(lb + off) = lo;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) xv[k] = tx[k] >= 0 ? cx[tx[k]] : 0.f;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    float hi = 0.f, lo = 0.f;
+                    if (tx[k] >= 0) {
+                        const double v = (double)xv[k] - mx;
+                        hi = __uint_as_float(to_tf32((float)v));
+                        lo = __uint_as_float(to_tf32((float)(v - (double)hi)));
+                    }
+                    const uint32_t off = cm_offset(tid, h16 + k);
+                    *reinterpret_cast<float *>(hb + off) = hi;
+                    *reinterpret_cast<float *>(lb + off) = lo;
+                }
             }
         }
         // stage B: 32 rows x 32 points, 8 values per thread
