@@ -14,8 +14,9 @@
 //
 // Targets are independent, so every round gathers the next request of every
 // unfinished target and evaluates all of them (candidates x surrogates x
-// targets) in one fused KSG launch, one permutation launch per request and one
-// statistics launch; only a few integers per request come back to the host.
+// targets) in one fused KSG launch per kernel class, one permutation launch per
+// request (per candidate with independent surrogates) and one statistics
+// launch; only a few integers per request come back to the host.
 #include <cuda_runtime.h>
 
 #include <algorithm>
