@@ -238,6 +238,11 @@ typedef struct {
                                       Fisher-Yates shuffle of the trials; inside trials: one
                                       Fisher-Yates shuffle per trial, trial 0 first, all drawn
                                       from one SplitMix64 stream keyed as the permutations */
+    int32_t estimator;             /* 0: KSG (above); 1: the linear-Gaussian estimator of
+                                      cmi_gauss (Methods, Vector autoregressive process), k
+                                      unused, theiler must be 0, every estimate at most 8 X
+                                      and 32 variables in all; decisions then compare the
+                                      FP64 estimates */
 } te_infer_params;
 
 typedef struct {
@@ -265,7 +270,8 @@ typedef struct {
 /*
  * Greedy multivariate TE network inference with hierarchical tests (Methods,
  * "Inference algorithm" steps 1-4 and "Statistical tests"), every CMI by the
- * KSG estimator above, every test by S permutation surrogates:
+ * KSG estimator above (or the Gaussian one, params->estimator), every test by S
+ * permutation surrogates:
  *   step 1 selects the target past by repeated maximum-statistic tests,
  *   step 2 selects the sources past conditioned on what was selected,
  *   step 3 prunes the sources past with minimum-statistic tests,

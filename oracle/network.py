@@ -44,7 +44,11 @@ notes):
     point (t = L .. T - 1 of trial 0, then of trial 1, ...); their
     surrogates shuffle the candidate's trial order when the R! orders cover
     the S surrogates, else its samples inside each trial (Statistical tests,
-    surrogate paragraph); no Theiler window is defined across trials.
+    surrogate paragraph); no Theiler window is defined across trials;
+  * estimator "gauss" runs the same four steps with the linear-Gaussian CMI
+    of oracle/gauss.py (Methods, Vector autoregressive process: the paper's
+    estimator for its VAR networks); its decisions compare the float64
+    estimates themselves, and it has no neighbour count or Theiler window.
 """
 from __future__ import annotations
 
@@ -53,7 +57,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import ksg
+from . import gauss, ksg
 
 STAGE_STANDALONE, STAGE_TARGET, STAGE_SOURCES, STAGE_PRUNE, STAGE_OMNIBUS, STAGE_SEQ = range(6)
 
@@ -75,6 +79,7 @@ class Params:
     seed: int = 0
     indep_surr: bool = False
     n_threads: int | None = None
+    estimator: str = "ksg"        # "ksg" or "gauss"
 
 
 @dataclass
@@ -134,8 +139,13 @@ def _shared_z_keys(v: _View, cand, z, p: Params, stage, it):
 def _group_keys(v: _View, cands_x, z, p: Params, perms):
     """Keys for every candidate (each a list of X variables of equal length)
     against Y = target present given Z, identity and every surrogate.
-    Returns int array [n_cand][1 + S] of Python ints."""
+    Returns int array [n_cand][1 + S] of Python ints (float64 estimates
+    with the Gaussian estimator)."""
     vm = v.vmap or (lambda u: tuple(u))
+    if p.estimator == "gauss":
+        zz = [vm(u) for u in z]
+        return [list(gauss.cmi_gauss(v.series, [vm(u) for u in c], [v.y], zz, max_lag=v.t0,
+                                     perms=perms)) for c in cands_x]
     n_c = len(cands_x)
     S = perms.shape[0]
     xs, pidx = [], []
@@ -189,6 +199,10 @@ def _resolve_theiler(series, p: Params) -> Params:
     """A negative window means automatic: the largest autocorrelation decay
     time over the processes (Supporting Information, dynamic correlation
     exclusion)."""
+    if p.estimator == "gauss":
+        if p.theiler != 0:
+            raise ValueError("the Gaussian estimator has no Theiler window")
+        return p
     if p.theiler >= 0:
         return p
     from dataclasses import replace
@@ -228,7 +242,9 @@ def infer_target(series, target: int, p: Params, trials=None) -> TargetResult:
         v = _View(pooled, target, (target * (t0 + 1), 0), 0, N,
                   vmap=lambda u: (u[0] * (t0 + 1) + u[1], 0),
                   trials=(R_, n, _trial_mode(trials, R_, p.n_surr)))
-    q, _ = ksg.digamma_q(N + 1)
+    if p.estimator not in ("ksg", "gauss"):
+        raise ValueError("estimator must be 'ksg' or 'gauss'")
+    q = ksg.digamma_q(N + 1)[0] if p.estimator == "ksg" else None
     res = TargetResult(target=target)
 
     # Step 1: target past
@@ -286,7 +302,7 @@ def infer_target(series, target: int, p: Params, trials=None) -> TargetResult:
         cnt = sum(1 for v in keys[1:] if v > kstar)
         pval = cnt / p.n_surr
         res.omnibus_key = kstar
-        res.omnibus_cmi = _i_from_key(kstar, q, p.k, N)
+        res.omnibus_cmi = float(kstar) if q is None else _i_from_key(kstar, q, p.k, N)
         res.omnibus_p = pval
         res.omnibus_tested = True
         res.significant = pval < p.alpha_omnibus
@@ -318,6 +334,35 @@ def infer_target(series, target: int, p: Params, trials=None) -> TargetResult:
     res.sel_sources = sorted(sel_x)
     res.significant = res.significant and bool(sel_x)
     return res
+
+
+def decision_margin(results) -> float:
+    """Smallest nonzero gap of a comparison that decided a test in the traces
+    of `results`: best against runner-up and observed against every surrogate
+    statistic (maximum, minimum and omnibus tests), neighbouring contributions
+    and contribution against null (step-down stage).  A second evaluation
+    whose estimates differ by less than half of it takes the same decisions;
+    exact ties (zero gaps) are left out, as identical inputs tie on both
+    sides."""
+    gaps = []
+    for r in results:
+        for stage, _it, _c, keys, null, _p, _d in r.trace:
+            orig = np.array([k[0] for k in keys], float)
+            if stage in (STAGE_TARGET, STAGE_SOURCES, STAGE_PRUNE):
+                srt = np.sort(orig)
+                low = stage == STAGE_PRUNE
+                if len(srt) > 1:
+                    gaps.append(srt[1] - srt[0] if low else srt[-1] - srt[-2])
+                gaps += list(np.abs(np.asarray(null, float) - (srt[0] if low else srt[-1])))
+            elif stage == STAGE_OMNIBUS:
+                k = np.asarray(keys[0], float)
+                gaps += list(np.abs(k[1:] - k[0]))
+            else:
+                gaps += list(np.diff(np.sort(orig)))
+                gaps += list(np.abs(np.asarray(null, float)[:, None] - orig[None, :]).ravel())
+    gaps = np.asarray(gaps, float)
+    gaps = gaps[gaps > 0]
+    return float(gaps.min()) if gaps.size else float("inf")
 
 
 def fdr_bh(pvals, alpha: float):

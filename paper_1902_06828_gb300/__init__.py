@@ -302,9 +302,11 @@ def te_network_infer(ctx: Context, data: Data, *, k=4, theiler=0, max_lag_target
                      max_lag_sources=5, n_surr=200, alpha_max=0.05, alpha_min=0.05,
                      alpha_omnibus=0.05, alpha_seq=0.05, seq_test=False, fdr=False,
                      alpha_fdr=0.05, seed=0, targets=None, indep_surr=False,
-                     surr_mode="auto") -> dict:
+                     surr_mode="auto", estimator="ksg") -> dict:
     """Greedy multivariate TE network inference; returns a dict with the
-    adjacency [src, tgt], min lags, per-target selections and counters."""
+    adjacency [src, tgt], min lags, per-target selections and counters.
+    estimator: "ksg" or "gauss" (the linear-Gaussian estimator of cmi_gauss;
+    k is then unused and theiler must be 0)."""
     tarr = None
     nt = 0
     if targets is not None:
@@ -314,7 +316,8 @@ def te_network_infer(ctx: Context, data: Data, *, k=4, theiler=0, max_lag_target
                          int(n_surr), float(alpha_max), float(alpha_min), float(alpha_omnibus),
                          float(alpha_seq), int(bool(seq_test)), int(bool(fdr)), float(alpha_fdr),
                          int(seed), C.cast(tarr, C.POINTER(C.c_int32)) if tarr else None, nt,
-                         int(bool(indep_surr)), {"auto": 0, "trials": 1, "within": 2}[surr_mode])
+                         int(bool(indep_surr)), {"auto": 0, "trials": 1, "within": 2}[surr_mode],
+                         {"ksg": 0, "gauss": 1}[estimator])
     res = C.POINTER(_abi.NetworkResult)()
     st = ctx._lib.te_network_infer(ctx._h, data._h, C.byref(P), C.byref(res))
     _check(ctx._h, st)

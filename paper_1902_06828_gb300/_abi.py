@@ -40,7 +40,8 @@ class InferParams(C.Structure):
                 ("alpha_omnibus", C.c_double), ("alpha_seq", C.c_double),
                 ("seq_test", C.c_int32), ("fdr", C.c_int32), ("alpha_fdr", C.c_double),
                 ("seed", C.c_uint64), ("targets", C.POINTER(C.c_int32)),
-                ("n_targets", C.c_int32), ("indep_surr", C.c_int32), ("surr_mode", C.c_int32)]
+                ("n_targets", C.c_int32), ("indep_surr", C.c_int32), ("surr_mode", C.c_int32),
+                ("estimator", C.c_int32)]
 
 
 class TargetResult(C.Structure):

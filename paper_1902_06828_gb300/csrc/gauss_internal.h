@@ -37,6 +37,12 @@ int gauss_cross_splits(int rows, int N);
 cudaError_t gauss_launch_stats(const GaussArgs &A, cudaStream_t st);
 cudaError_t gauss_launch_cross_tc(const GaussArgs &A, cudaStream_t st);
 double gauss_tc_gamma();   // relative error factor of the tensor-core contraction
+// the same cross-covariances with FP64 products and sums on the CUDA cores
+cudaError_t gauss_launch_cross_f64(const GaussArgs &A, cudaStream_t st);
+double gauss_f64_gamma(int N);   // relative error factor of the FP64 contraction
 cudaError_t gauss_launch_schur(const GaussArgs &A, double gamma, cudaStream_t st);
+// keys[2i], keys[2i + 1] = order-preserving int128 (hi, lo) of v[i]; a value
+// that is not finite sets *bad
+cudaError_t gauss_launch_keys(const double *v, int n, long long *keys, int *bad, cudaStream_t st);
 
 }  // namespace teksg

@@ -502,7 +502,80 @@ __global__ void gauss_cross_reduce_kernel(GaussArgs A)
     A.cross[e] = s * (1.0 / (double)(A.N - 1));
 }
 
+// FP64 cross-covariance on the CUDA cores, for estimates whose decisions must
+// agree with an FP64 evaluation down to near-ties (network inference): the same
+// sums as the tensor-core kernel, every product and addition in FP64.  One
+// thread per row (surrogate s, X dim a) holds its dw sums in registers; the
+// block stages the centred W values of each 32-point chunk in shared memory
+// (read as broadcasts) and each thread gathers its permuted X values.  Grid y
+// splits the points exactly as the tensor-core kernel does, and the same
+// reduction adds the splits in order.
+constexpr int kF64Rows = 128;
+__global__ void __launch_bounds__(kF64Rows) gauss_cross_f64_kernel(GaussArgs A)
+{
+    __shared__ double sW[kGaussKC][kGaussMaxDims];
+    const int rows = (A.S + 1) * A.dx, dw = A.dw;
+    const int row = blockIdx.x * kF64Rows + threadIdx.x;
+    const bool live = row < rows;
+    const int s = live ? row / A.dx : 0, a = live ? row % A.dx : 0;
+    const int32_t *pi = s > 0 ? A.perms + (size_t)(s - 1) * A.N : nullptr;
+    const float *xcol = A.base + A.cols[a];
+    const double mx = A.mean[a];
+    double acc[kGaussMaxDims];
+#pragma unroll
+    for (int w = 0; w < kGaussMaxDims; ++w) acc[w] = 0.0;
+    const int nchunks = (A.N + kGaussKC - 1) / kGaussKC;
+    const int c0 = blockIdx.y * A.chunks_per_split;
+    const int c1 = min(nchunks, c0 + A.chunks_per_split);
+    for (int c = c0; c < c1; ++c) {
+        const int t0 = c * kGaussKC, n = min(kGaussKC, A.N - t0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < n * dw; e += kF64Rows) {
+            const int t = e / dw, w = e - t * dw;
+            sW[t][w] = (double)A.base[A.cols[A.dx + w] + t0 + t] - A.mean[A.dx + w];
+        }
+        __syncthreads();
+        if (!live) continue;
+#pragma unroll 4
+        for (int t = 0; t < n; ++t) {
+            const int src = pi ? pi[t0 + t] : t0 + t;
+            const double xv = (double)xcol[src] - mx;
+#pragma unroll
+            for (int w = 0; w < kGaussMaxDims; ++w)
+                if (w < dw) acc[w] = fma(xv, sW[t][w], acc[w]);
+        }
+    }
+    if (!live) return;
+    double *dst = A.cross_part + ((size_t)blockIdx.y * rows + row) * dw;
+#pragma unroll
+    for (int w = 0; w < kGaussMaxDims; ++w)
+        if (w < dw) dst[w] = acc[w];
+}
+
+// Order-preserving integer image of the estimates, in the (hi, lo) int128 form
+// the test-statistics kernel compares: key(a) < key(b) exactly when a < b
+// (sign-magnitude bits turned into two's complement order; -0 taken as +0).
+// A value that is not finite (a singular Schur complement) sets *bad.
+__global__ void gauss_keys_kernel(const double *v, int n, long long *keys, int *bad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x = v[i] + 0.0;
+    if (!isfinite(x)) *bad = 1;
+    const long long b = __double_as_longlong(x);
+    const long long k = b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+    keys[2 * (size_t)i] = k < 0 ? -1 : 0;
+    keys[2 * (size_t)i + 1] = k;
+}
+
 }  // namespace
+
+cudaError_t gauss_launch_keys(const double *v, int n, long long *keys, int *bad, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    gauss_keys_kernel<<<(n + 255) / 256, 256, 0, st>>>(v, n, keys, bad);
+    return cudaGetLastError();
+}
 
 int gauss_cross_splits(int rows, int N)
 {
@@ -535,6 +608,27 @@ cudaError_t gauss_launch_cross_tc(const GaussArgs &A, cudaStream_t st)
     const long long total = (long long)rows * A.dw;
     gauss_cross_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(A);
     return cudaGetLastError();
+}
+
+cudaError_t gauss_launch_cross_f64(const GaussArgs &A, cudaStream_t st)
+{
+    const int rows = (A.S + 1) * A.dx;
+    if (A.splits < 1 || A.splits > 65535) return cudaErrorInvalidValue;
+    gauss_cross_f64_kernel<<<dim3((rows + kF64Rows - 1) / kF64Rows, A.splits), kF64Rows, 0, st>>>(
+        A);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long total = (long long)rows * A.dw;
+    gauss_cross_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
+double gauss_f64_gamma(int N)
+{
+    // a sum of N FP64 products, |error| <= gamma_N sum |x||w| with
+    // gamma_N = N u / (1 - N u), u = 2^-53, plus the centring roundings
+    const double nu = (double)(N + 2) * std::ldexp(1.0, -53);
+    return nu / (1.0 - nu);
 }
 
 double gauss_tc_gamma()

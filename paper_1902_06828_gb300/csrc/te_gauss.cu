@@ -1,15 +1,167 @@
 // cmi_gauss: linear-Gaussian CMI of one estimate and its permutation
-// surrogates (the estimator the paper uses for its VAR networks).
+// surrogates (the estimator the paper uses for its VAR networks), and the same
+// pipeline over the groups of a network-inference round.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "gauss_internal.h"
 #include "te_runtime.h"
 
 using namespace teksg;
+
+namespace {
+
+// Shape of one estimate (N points, S surrogates, X / Y / Z dimensions) and the
+// number of doubles of its workspace: means, covariance, the two Cholesky
+// factors, their inverse norms, scratch, the cross-covariances and their
+// per-split partial sums.  The estimates and error bounds are bound elsewhere.
+size_t gauss_shape(GaussArgs &A, int N, int S, int dx, int dy, int dz)
+{
+    A.N = N;
+    A.S = S;
+    A.dx = dx;
+    A.dy = dy;
+    A.dw = dy + dz;
+    A.d = dx + dy + dz;
+    const int nchunks = (N + 31) / 32;
+    const int splits = gauss_cross_splits((S + 1) * dx, N);
+    A.chunks_per_split = (nchunks + splits - 1) / splits;
+    A.splits = (nchunks + A.chunks_per_split - 1) / A.chunks_per_split;
+    const size_t d = (size_t)A.d, dw = (size_t)A.dw;
+    return d + d * d + 2 * dw * dw + 2 + kGaussMaxDims +
+           (size_t)(S + 1) * dx * dw * (1 + (size_t)A.splits);
+}
+
+// workspace pointers of a shaped estimate, starting at w
+void gauss_bind(GaussArgs &A, double *w)
+{
+    const size_t d = (size_t)A.d, dw = (size_t)A.dw;
+    A.mean = w;
+    A.cov = A.mean + d;
+    A.LW = A.cov + d * d;
+    A.LZ = A.LW + dw * dw;
+    A.norms = A.LZ + dw * dw;
+    A.scratch = A.norms + 2;
+    A.cross = A.scratch + kGaussMaxDims;
+    A.cross_part = A.cross + (size_t)(A.S + 1) * A.dx * dw;
+}
+
+// offset of variable v's column at the first point: the value at point t is
+// series[col + t]
+int gauss_col(const te_data *data, int max_lag, te_var v)
+{
+    return v.proc * data->T + max_lag - v.lag;
+}
+
+}  // namespace
+
+namespace teksg {
+
+double gauss_key_value(int64_t hi, uint64_t lo)
+{
+    (void)hi;   // the key is the sign extension of lo
+    const long long k = (long long)lo;
+    const long long b = k >= 0 ? k : (k ^ 0x7fffffffffffffffLL);
+    double v;
+    std::memcpy(&v, &b, 8);
+    return v;
+}
+
+te_status run_groups_gauss(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_out)
+{
+    // One estimate per candidate of a group: its members share X, Y, Z and
+    // differ only in the permutation.  Member s of a candidate writes slot
+    // slot0 + s and, for s >= 1, reads permutation perms + (s - 1) N.  The
+    // test decisions compare these estimates, so the cross-covariances are
+    // summed in FP64 (gauss_launch_cross_f64): decisions then agree with an
+    // FP64 evaluation except at ties closer than ~1e-12, where the split-TF32
+    // contraction of cmi_gauss (~1e-7) would flip near-ties.
+    struct Est {
+        const HostGroup *g;
+        int xc, S, slot0;
+        const int32_t *perms;
+        size_t col0;
+    };
+    std::vector<Est> est;
+    std::vector<int> cols;
+    size_t ws = 0;
+    for (const HostGroup &g : groups) {
+        const int N = g.data->T - g.max_lag;
+        const int dy = (int)g.y.size(), dz = (int)g.z.size();
+        if (g.dx > kGaussMaxX || g.dx + dy + dz > kGaussMaxDims)
+            return fail(ctx, TE_EINVAL, "the Gaussian estimator takes dx <= 8 and dx + dy + dz <= 32");
+        if (N <= g.dx + dy + dz + 1)
+            return fail(ctx, TE_EINVAL, "need more points than variables + 1");
+        std::map<int, std::vector<const HostMember *>> by;
+        for (const HostMember &m : g.members) by[m.xcol_first].push_back(&m);
+        for (auto &kv : by) {
+            auto &ms = kv.second;
+            std::sort(ms.begin(), ms.end(),
+                      [](const HostMember *a, const HostMember *b) { return a->out < b->out; });
+            const int S = (int)ms.size() - 1;
+            const int32_t *p1 = S > 0 ? ms[1]->perm : nullptr;
+            bool ok = ms[0]->perm == nullptr;
+            for (int s = 1; s <= S && ok; ++s)
+                ok = ms[s]->out == ms[0]->out + s && ms[s]->perm == p1 + (size_t)(s - 1) * N;
+            if (!ok)
+                return fail(ctx, TE_EINTERNAL,
+                            "Gaussian estimates need consecutive slots and permutations");
+            est.push_back(Est{&g, kv.first, S, ms[0]->out, p1, cols.size()});
+            for (int a = 0; a < g.dx; ++a)
+                cols.push_back(gauss_col(g.data, g.max_lag, g.xvars[kv.first + a]));
+            for (const te_var &v : g.y) cols.push_back(gauss_col(g.data, g.max_lag, v));
+            for (const te_var &v : g.z) cols.push_back(gauss_col(g.data, g.max_lag, v));
+            GaussArgs A{};
+            ws = std::max(ws, gauss_shape(A, N, S, g.dx, dy, dz));
+        }
+    }
+    // doubles: shared per-estimate workspace, then estimates and bounds of all
+    // slots; ints: status flags, then the columns of every estimate
+    const size_t nd = ws + 2 * (size_t)n_out;
+    te_status st;
+    if ((st = ensure_dev(ctx, ctx->ws_gauss, nd * 8 + (2 + cols.size()) * 4))) return st;
+    if ((st = ensure_dev(ctx, ctx->ws_keys, (size_t)std::max(n_out, 1) * 16))) return st;
+    double *w = (double *)ctx->ws_gauss.p;
+    double *v_out = w + ws, *v_err = v_out + n_out;
+    int *status = (int *)(w + nd), *cols_dev = status + 2;
+    CK(cudaMemsetAsync(status, 0, 2 * sizeof(int), ctx->stream), "cudaMemsetAsync");
+    CK(cudaMemsetAsync(v_out, 0, (size_t)n_out * 8, ctx->stream), "cudaMemsetAsync");
+    if (!cols.empty())
+        CK(copy_h2d(ctx, cols_dev, cols.data(), cols.size() * 4), "cudaMemcpyAsync");
+    for (const Est &e : est) {
+        const HostGroup &g = *e.g;
+        GaussArgs A{};
+        gauss_shape(A, g.data->T - g.max_lag, e.S, g.dx, (int)g.y.size(), (int)g.z.size());
+        gauss_bind(A, w);
+        A.base = g.data->d_series;
+        A.cols = cols_dev + e.col0;
+        A.perms = e.perms;
+        A.status = status;
+        A.out = v_out + e.slot0;
+        A.err = v_err + e.slot0;
+        CK(gauss_launch_stats(A, ctx->stream), "Gaussian statistics launch");
+        CK(gauss_launch_cross_f64(A, ctx->stream), "FP64 cross-covariance launch");
+        CK(gauss_launch_schur(A, gauss_f64_gamma(A.N), ctx->stream), "Schur launch");
+        ctx->stats.launches += 6;
+        ctx->stats.estimates += (uint64_t)e.S + 1;
+    }
+    CK(gauss_launch_keys(v_out, n_out, (long long *)ctx->ws_keys.p, status, ctx->stream),
+       "key launch");
+    ctx->stats.launches++;
+    int flags[2] = {0, 0};
+    CK(copy_d2h(ctx, flags, status, sizeof flags), "cudaMemcpyAsync");
+    CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    if (flags[1]) return fail(ctx, TE_ETIMEOUT, "tensor-core contraction did not complete in time");
+    if (flags[0]) return fail(ctx, TE_EINVAL, "a covariance block of an estimate is singular");
+    return TE_OK;
+}
+
+}  // namespace teksg
 
 extern "C" te_status cmi_gauss(te_ctx *ctx, const te_data *data, const te_var *x, int32_t dx,
                                const te_var *y, int32_t dy, const te_var *z, int32_t dz,
@@ -25,48 +177,29 @@ extern "C" te_status cmi_gauss(te_ctx *ctx, const te_data *data, const te_var *x
             return st;
         if (dx > kGaussMaxX) return fail(ctx, TE_EINVAL, "cmi_gauss supports dx <= 8");
         const int N = data->T - p->max_lag, S = p->n_surr;
-        const int d = dx + dy + dz, dw = dy + dz;
+        const int d = dx + dy + dz;
         if (N <= d + 1) return fail(ctx, TE_EINVAL, "need more points than variables + 1");
         CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-        // workspace layout (doubles first, then ints)
-        const int splits = gauss_cross_splits((S + 1) * dx, N);
-        const int nchunks = (N + 31) / 32;
-        const size_t nd = (size_t)d + (size_t)d * d + 2 * (size_t)dw * dw + 2 + kGaussMaxDims +
-                          (size_t)(S + 1) * dx * dw * (1 + (size_t)splits) + 2 * (size_t)(S + 1);
-        const size_t bytes = nd * 8 + (size_t)(d + 8) * 4;
-        if ((st = ensure_dev(ctx, ctx->ws_gauss, bytes))) return st;
+        // workspace: the estimate's doubles, its estimates and bounds, then ints
+        GaussArgs A{};
+        const size_t ws = gauss_shape(A, N, S, dx, dy, dz);
+        const size_t nd = ws + 2 * (size_t)(S + 1);
+        if ((st = ensure_dev(ctx, ctx->ws_gauss, nd * 8 + (size_t)(d + 8) * 4))) return st;
         if ((st = ensure_dev(ctx, ctx->ws_perm, (size_t)std::max(S, 1) * N * 4))) return st;
         double *w = (double *)ctx->ws_gauss.p;
-        GaussArgs A{};
+        gauss_bind(A, w);
         A.base = data->d_series;
-        A.N = N;
-        A.S = S;
-        A.dx = dx;
-        A.dy = dy;
-        A.dw = dw;
-        A.d = d;
         A.perms = (const int32_t *)ctx->ws_perm.p;
-        A.mean = w;
-        A.cov = A.mean + d;
-        A.LW = A.cov + (size_t)d * d;
-        A.LZ = A.LW + (size_t)dw * dw;
-        A.norms = A.LZ + (size_t)dw * dw;
-        A.scratch = A.norms + 2;
-        A.cross = A.scratch + kGaussMaxDims;
-        A.out = A.cross + (size_t)(S + 1) * dx * dw;
+        A.out = w + ws;
         A.err = A.out + (S + 1);
-        A.cross_part = A.err + (S + 1);
-        A.splits = splits;
-        A.chunks_per_split = (nchunks + splits - 1) / splits;
-        A.splits = (nchunks + A.chunks_per_split - 1) / A.chunks_per_split;
-        int *ip = (int *)(A.cross_part + (size_t)splits * (S + 1) * dx * dw);
+        int *ip = (int *)(w + nd);
         A.status = ip;
         int *cols_dev = ip + 2;
         A.cols = cols_dev;
         std::vector<int> cols;
-        for (int a = 0; a < dx; ++a) cols.push_back(x[a].proc * data->T + p->max_lag - x[a].lag);
-        for (int a = 0; a < dy; ++a) cols.push_back(y[a].proc * data->T + p->max_lag - y[a].lag);
-        for (int a = 0; a < dz; ++a) cols.push_back(z[a].proc * data->T + p->max_lag - z[a].lag);
+        for (int a = 0; a < dx; ++a) cols.push_back(gauss_col(data, p->max_lag, x[a]));
+        for (int a = 0; a < dy; ++a) cols.push_back(gauss_col(data, p->max_lag, y[a]));
+        for (int a = 0; a < dz; ++a) cols.push_back(gauss_col(data, p->max_lag, z[a]));
         CK(copy_h2d(ctx, cols_dev, cols.data(), cols.size() * 4), "cudaMemcpyAsync");
         CK(launch_perms((int32_t *)ctx->ws_perm.p, N, N, p->seed, p->stream_tag, 0, 0, 1, S,
                         ctx->stream),

@@ -16,7 +16,10 @@
 // unfinished target and evaluates all of them (candidates x surrogates x
 // targets) in one fused KSG launch per kernel class, one permutation launch per
 // request (per candidate with independent surrogates) and one statistics
-// launch; only a few integers per request come back to the host.
+// launch; only a few integers per request come back to the host.  With the
+// linear-Gaussian estimator each candidate's estimate and surrogates run
+// through cmi_gauss's kernels instead, and the statistics compare the
+// estimates' order-preserving integer images.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -114,6 +117,11 @@ te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_para
         if (!data || !params || !out) return fail(ctx, TE_EINVAL, "NULL argument");
         if (data->ctx != ctx) return fail(ctx, TE_EINVAL, "data belongs to another context");
         te_infer_params P = *params;
+        if (P.estimator != 0 && P.estimator != 1)
+            return fail(ctx, TE_EINVAL, "estimator must be 0 (KSG) or 1 (Gaussian)");
+        const bool gauss = P.estimator == 1;
+        if (gauss && P.theiler != 0)
+            return fail(ctx, TE_EINVAL, "the Gaussian estimator has no Theiler window");
         // pooled replications: candidates over the original processes, every
         // variable (p, l) read from the pooled row p * (L + 1) + l at lag 0
         const bool pooled = data->emb_lag >= 0;
@@ -125,7 +133,8 @@ te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_para
             return fail(ctx, TE_EINVAL, "surr_mode must be 0, 1 or 2");
         if (P.max_lag_target < 1 || P.max_lag_sources < 1)
             return fail(ctx, TE_EINVAL, "max lags must be >= 1");
-        if (P.k < 1 || P.k > TE_MAX_K) return fail(ctx, TE_EINVAL, "k must be in 1..16");
+        if (!gauss && (P.k < 1 || P.k > TE_MAX_K))
+            return fail(ctx, TE_EINVAL, "k must be in 1..16");
         if (P.theiler < 0) {   // automatic window: largest decay time over the processes
             CK(cudaSetDevice(ctx->device), "cudaSetDevice");
             int32_t w = 0;
@@ -162,7 +171,7 @@ te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_para
             for (int r = 2; r <= data->n_rep; ++r) orders *= r;
             trial_mode = P.surr_mode == 1 ? 0 : P.surr_mode == 2 ? 1 : (orders >= S ? 0 : 1);
         }
-        if ((long long)N - 1 - 2LL * P.theiler < P.k)
+        if (!gauss && (long long)N - 1 - 2LL * P.theiler < P.k)
             return fail(ctx, TE_EINVAL, "fewer than k valid neighbours for some point");
         std::vector<int> targets;
         if (P.targets) {
@@ -297,7 +306,9 @@ te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_para
                 reqs.push_back(StatReq{(long long)t.out_base, t.n_cand, S, t.mode, t.cnt_off,
                                        t.orig_off});
             }
-            if ((st = run_groups(ctx, groups, n_out))) return st;
+            if ((st = gauss ? run_groups_gauss(ctx, groups, n_out)
+                            : run_groups(ctx, groups, n_out)))
+                return st;
 
             // ---- statistics on the device, small readback ----
             const size_t req_bytes = reqs.size() * sizeof(StatReq);
@@ -351,7 +362,8 @@ te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_para
                 } else if (t.stage == ST_OMNIBUS) {
                     const double p = (double)cnt[0] / S;
                     const long long *kk = ob + 2 * t.orig_off;
-                    t.omni_cmi = key_to_cmi(ctx, kk[0], (uint64_t)kk[1], P.k, N);
+                    t.omni_cmi = gauss ? gauss_key_value(kk[0], (uint64_t)kk[1])
+                                       : key_to_cmi(ctx, kk[0], (uint64_t)kk[1], P.k, N);
                     t.omni_p = p;
                     t.omni_tested = 1;
                     t.significant = p < P.alpha_omnibus;

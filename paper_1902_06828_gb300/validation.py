@@ -12,11 +12,13 @@
 
 Networks come from the seeded generators in synth (random Erdos-Renyi
 topology with link probability p = 3 / N; the paper's VAR or coupled logistic
-map dynamics); every estimate is the KSG estimator of te_network_infer (the
-paper used its Gaussian estimator for the VAR runs).
+map dynamics); the estimates are te_network_infer's KSG estimator, or with
+--estimator gauss its linear-Gaussian one (the paper's choice for the VAR
+runs).
 
     python -m paper_1902_06828_gb300.validation --e1 --dynamics var \\
-        --sizes 10 40 --lengths 1000 10000 --sims 2 --surr 200 --alpha 0.05
+        --sizes 10 40 --lengths 1000 10000 --sims 2 --surr 200 --alpha 0.05 \\
+        --estimator gauss
     python -m paper_1902_06828_gb300.validation --e2 --sizes 10 --alphas 0.05 0.01 \\
         --sims 20 --lengths 10000 --surr 200
 
@@ -78,15 +80,16 @@ def _network(dynamics: str, n: int, T: int, seed: int, empty: bool = False):
     return synth.standardise_jitter(x, seed), adj
 
 
-def _infer(te, ctx, series, alpha, n_surr, seed, theiler=0):
+def _infer(te, ctx, series, alpha, n_surr, seed, theiler=0, estimator="ksg"):
     data = te.te_data_create(ctx, series)
     return te.te_network_infer(ctx, data, k=4, theiler=theiler, max_lag_target=5,
                                max_lag_sources=5, n_surr=n_surr, alpha_max=alpha,
-                               alpha_min=alpha, alpha_omnibus=alpha, seed=seed)
+                               alpha_min=alpha, alpha_omnibus=alpha, seed=seed,
+                               estimator=estimator)
 
 
 def run_e1(ctx, dynamics="var", sizes=(10,), lengths=(1000,), n_sims=1, alpha=0.05,
-           n_surr=200, seed=0, out=print):
+           n_surr=200, seed=0, out=print, estimator="ksg"):
     """Precision / recall / specificity over (size, length, simulation)."""
     import paper_1902_06828_gb300 as te
     rows = []
@@ -95,9 +98,10 @@ def run_e1(ctx, dynamics="var", sizes=(10,), lengths=(1000,), n_sims=1, alpha=0.
             for s in range(n_sims):
                 series, adj = _network(dynamics, n, T, seed + 1000 * s + n)
                 t0 = time.time()
-                g = _infer(te, ctx, series, alpha, n_surr, seed + s)
-                row = dict(test="e1", dynamics=dynamics, n=n, T=T, sim=s, alpha=alpha,
-                           n_surr=n_surr, links=int(adj.sum()), seconds=time.time() - t0,
+                g = _infer(te, ctx, series, alpha, n_surr, seed + s, estimator=estimator)
+                row = dict(test="e1", dynamics=dynamics, estimator=estimator, n=n, T=T, sim=s,
+                           alpha=alpha, n_surr=n_surr, links=int(adj.sum()),
+                           seconds=time.time() - t0,
                            n_estimates=g["n_estimates"], **scores(adj, g["adjacency"]))
                 rows.append(row)
                 out(json.dumps(row))
@@ -105,7 +109,7 @@ def run_e1(ctx, dynamics="var", sizes=(10,), lengths=(1000,), n_sims=1, alpha=0.
 
 
 def run_e2(ctx, dynamics="var", sizes=(10,), alphas=(0.05,), n_sims=10, T=10000, n_surr=200,
-           seed=0, out=print):
+           seed=0, out=print, estimator="ksg"):
     """False positive rate per target on empty networks, with its expected range."""
     import paper_1902_06828_gb300 as te
     rows = []
@@ -114,10 +118,11 @@ def run_e2(ctx, dynamics="var", sizes=(10,), alphas=(0.05,), n_sims=10, T=10000,
             rates = []
             for s in range(n_sims):
                 series, _ = _network(dynamics, n, T, seed + 1000 * s + n, empty=True)
-                g = _infer(te, ctx, series, alpha, n_surr, seed + s)
+                g = _infer(te, ctx, series, alpha, n_surr, seed + s, estimator=estimator)
                 rates.append(fpr_target(g["adjacency"]))
             lo, hi = fpr_expected_range(n, alpha, n_sims)
-            row = dict(test="e2", dynamics=dynamics, n=n, T=T, alpha=alpha, n_surr=n_surr,
+            row = dict(test="e2", dynamics=dynamics, estimator=estimator, n=n, T=T, alpha=alpha,
+                       n_surr=n_surr,
                        sims=n_sims, fpr_target=float(np.mean(rates)), expected_p05=lo,
                        expected_p95=hi, within=bool(lo <= np.mean(rates) <= hi))
             rows.append(row)
@@ -137,20 +142,23 @@ def main(argv=None):
     ap.add_argument("--sims", type=int, default=1)
     ap.add_argument("--surr", type=int, default=200)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--estimator", default="ksg", choices=("ksg", "gauss"))
     a = ap.parse_args(argv)
     import paper_1902_06828_gb300 as te
     ctx = te.Context(0)
     if a.e1:
-        rows = run_e1(ctx, a.dynamics, a.sizes, a.lengths, a.sims, a.alpha, a.surr, a.seed)
+        rows = run_e1(ctx, a.dynamics, a.sizes, a.lengths, a.sims, a.alpha, a.surr, a.seed,
+                      estimator=a.estimator)
         for n in a.sizes:
             for T in a.lengths:
                 rs = [r for r in rows if r["n"] == n and r["T"] == T]
                 mean = {k: float(np.mean([r[k] for r in rs if r[k] is not None] or [np.nan]))
                         for k in ("precision", "recall", "specificity")}
-                print(json.dumps(dict(test="e1_summary", dynamics=a.dynamics, n=n, T=T,
-                                      sims=len(rs), **mean)))
+                print(json.dumps(dict(test="e1_summary", dynamics=a.dynamics,
+                                      estimator=a.estimator, n=n, T=T, sims=len(rs), **mean)))
     if a.e2:
-        run_e2(ctx, a.dynamics, a.sizes, a.alphas, a.sims, a.lengths[0], a.surr, a.seed)
+        run_e2(ctx, a.dynamics, a.sizes, a.alphas, a.sims, a.lengths[0], a.surr, a.seed,
+               estimator=a.estimator)
     ctx.close()
 
 

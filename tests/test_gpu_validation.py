@@ -52,3 +52,26 @@ def test_empty_network_false_positive_rate_over_50_seeds(ctx):
                       seed=11, out=lambda s: None)
     lo, hi = val.fpr_expected_range(10, 0.05, 50, q=(0.001, 0.999))
     assert lo <= rows[0]["fpr_target"] <= hi, rows[0]
+
+
+def test_e1_gaussian_scores_match_oracle(ctx):
+    # the paper's estimator for its VAR runs; decisions compare FP64 estimates,
+    # so the case first checks the oracle's closest deciding gap
+    rows = val.run_e1(ctx, "var", sizes=(6,), lengths=(1500,), n_sims=1, alpha=0.1, n_surr=40,
+                      seed=5, out=lambda s: None, estimator="gauss")
+    series, adj = val._network("var", 6, 1500, 5 + 6)
+    p = onet.Params(max_lag_target=5, max_lag_sources=5, n_surr=40, alpha_max=0.1,
+                    alpha_min=0.1, alpha_omnibus=0.1, seed=5, estimator="gauss")
+    adj_o, res_o = onet.infer_network(series, p)
+    assert onet.decision_margin(res_o) > 1e-9
+    want = val.scores(adj, adj_o)
+    for key in ("tp", "fp", "tn", "fn"):
+        assert rows[0][key] == want[key]
+
+
+def test_empty_network_false_positive_rate_gaussian_over_50_seeds(ctx):
+    # as above with the Gaussian estimator
+    rows = val.run_e2(ctx, "var", sizes=(10,), alphas=(0.05,), n_sims=50, T=1000, n_surr=100,
+                      seed=11, out=lambda s: None, estimator="gauss")
+    lo, hi = val.fpr_expected_range(10, 0.05, 50, q=(0.001, 0.999))
+    assert lo <= rows[0]["fpr_target"] <= hi, rows[0]
