@@ -37,9 +37,19 @@ int gauss_cross_splits(int rows, int N);
 cudaError_t gauss_launch_stats(const GaussArgs &A, cudaStream_t st);
 cudaError_t gauss_launch_cross_tc(const GaussArgs &A, cudaStream_t st);
 double gauss_tc_gamma();   // relative error factor of the tensor-core contraction
-// the same cross-covariances with FP64 products and sums on the CUDA cores
-cudaError_t gauss_launch_cross_f64(const GaussArgs &A, cudaStream_t st);
-double gauss_f64_gamma(int N);   // relative error factor of the FP64 contraction
+// relative error factor of the FP64 contraction: a sum of N FP64 products
+// errs by at most gamma_N sum |x||w|, gamma_N = N u / (1 - N u), u = 2^-53
+// (N + 2 for the centring roundings)
+__host__ __device__ inline double gauss_f64_gamma(int N)
+{
+    const double nu = (double)(N + 2) * 0x1p-53;
+    return nu / (1.0 - nu);
+}
+// the whole FP64 pipeline (means, covariance, factors, FP64 contraction and
+// its reduction, Schur complements) for n <= 65535 estimates in one launch
+// per kernel: estimate i's arguments at args_dev[i] (device) and args_host[i]
+cudaError_t gauss_launch_batch_f64(const GaussArgs *args_dev, const GaussArgs *args_host, int n,
+                                   cudaStream_t st);
 cudaError_t gauss_launch_schur(const GaussArgs &A, double gamma, cudaStream_t st);
 // keys[2i], keys[2i + 1] = order-preserving int128 (hi, lo) of v[i]; a value
 // that is not finite sets *bad

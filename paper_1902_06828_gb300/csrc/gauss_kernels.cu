@@ -13,6 +13,7 @@
 #include <math_constants.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "gauss_internal.h"
@@ -36,10 +37,9 @@ __device__ __forceinline__ double block_sum(double v, double *red)
 }
 
 // column means: block d
-__global__ void gauss_mean_kernel(GaussArgs A)
+__device__ __forceinline__ void gauss_mean_body(const GaussArgs &A, int d)
 {
     __shared__ double red[32];
-    const int d = blockIdx.x;
     const float *col = A.base + A.cols[d];
     double s = 0.0;
     for (int t = threadIdx.x; t < A.N; t += blockDim.x) s += (double)col[t];
@@ -47,11 +47,11 @@ __global__ void gauss_mean_kernel(GaussArgs A)
     if (threadIdx.x == 0) A.mean[d] = s / (double)A.N;
 }
 
-// covariance of columns (i, j), i <= j: block = pair index
-__global__ void gauss_cov_kernel(GaussArgs A)
+// covariance of columns (i, j), i <= j: block = pair index p
+__device__ __forceinline__ void gauss_cov_body(const GaussArgs &A, int p)
 {
     __shared__ double red[32];
-    int p = blockIdx.x, i = 0;
+    int i = 0;
     while (p >= A.d - i) {
         p -= A.d - i;
         ++i;
@@ -157,11 +157,12 @@ __device__ double inv_frob2_warp(const double *L, int n, int ld, double (*col)[3
 
 // Factor S_ZZ and S_WW (one warp).  W = the Y then Z columns; Z is the
 // trailing block of W.  Writes L_W, L_Z (lower, row-major, ld = dw) and
-// ||L^-1||_F^2 of each; status[0] = 1 if a block is not positive definite.
-__global__ void gauss_factor_kernel(GaussArgs A)
+// ||L^-1||_F^2 of each; status[0] = 1 if a block is not positive definite
+// (never cleared here, so estimates sharing a status word accumulate it).
+__device__ __forceinline__ void gauss_factor_body(const GaussArgs &A)
 {
     __shared__ double col[32][33];
-    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    if (threadIdx.x >= 32) return;
     const int lane = threadIdx.x;
     const int dx = A.dx, dw = A.dw, dy = A.dy, dz = dw - dy, d = A.d;
     for (int e = lane; e < dw * dw; e += 32) {
@@ -172,7 +173,7 @@ __global__ void gauss_factor_kernel(GaussArgs A)
     __syncwarp();
     bool ok = chol_warp(A.LW, dw, dw);
     if (dz > 0) ok = ok && chol_warp(A.LZ, dz, dw);
-    if (lane == 0) A.status[0] = ok ? 0 : 1;
+    if (lane == 0 && !ok) A.status[0] = 1;
     if (!ok) return;
     __syncwarp();
     const double nw = inv_frob2_warp(A.LW, dw, dw, col);
@@ -187,9 +188,8 @@ __global__ void gauss_factor_kernel(GaussArgs A)
 // Per surrogate (one thread): Schur complements given Z and given W, their
 // log-determinants, the estimate and a first-order bound on its error from
 // the cross-covariance error model |dS_XW_ij| <= gamma sqrt(S_ii S_jj).
-__global__ void gauss_schur_kernel(GaussArgs A, double gamma)
+__device__ __forceinline__ void gauss_schur_body(const GaussArgs &A, double gamma, int s)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s > A.S) return;
     const int dx = A.dx, dw = A.dw, dy = A.dy, dz = dw - dy, d = A.d;
     const double *c = A.cross + (size_t)s * dx * dw;   // [dx][dw]
@@ -492,10 +492,9 @@ __global__ void __launch_bounds__(128, 1) gauss_cross_tc_kernel(GaussArgs A)
 }
 
 // cross = (sum of the splits' partial sums, in split order) / (N - 1)
-__global__ void gauss_cross_reduce_kernel(GaussArgs A)
+__device__ __forceinline__ void gauss_cross_reduce_body(const GaussArgs &A, long long e)
 {
     const long long total = (long long)(A.S + 1) * A.dx * A.dw;
-    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= total) return;
     double s = 0.0;
     for (int p = 0; p < A.splits; ++p) s += A.cross_part[(size_t)p * total + e];
@@ -507,32 +506,38 @@ __global__ void gauss_cross_reduce_kernel(GaussArgs A)
 // sums as the tensor-core kernel, every product and addition in FP64.  One
 // thread per row (surrogate s, X dim a) holds its dw sums in registers; the
 // block stages the centred W values of each 32-point chunk in shared memory
-// (read as broadcasts) and each thread gathers its permuted X values.  Grid y
-// splits the points exactly as the tensor-core kernel does, and the same
-// reduction adds the splits in order.
+// (read as broadcasts) and each thread gathers its permuted X values.  The
+// points are split into A.splits ranges of chunks_per_split chunks (grid y),
+// and the tensor-core kernel's reduction adds the splits in order.
 constexpr int kF64Rows = 128;
-__global__ void __launch_bounds__(kF64Rows) gauss_cross_f64_kernel(GaussArgs A)
+// DW4 = dw rounded up to a multiple of 4: the W values past dw are staged as
+// zeros, so the inner loop has no per-column guard (a guarded loop unrolled to
+// the 32-column maximum would issue 32 FP64 FMAs per point whatever dw is).
+template <int DW4>
+__device__ __forceinline__ void gauss_cross_f64_body(const GaussArgs &A, int bx, int by,
+                                                     double (*sW)[kGaussMaxDims])
 {
-    __shared__ double sW[kGaussKC][kGaussMaxDims];
     const int rows = (A.S + 1) * A.dx, dw = A.dw;
-    const int row = blockIdx.x * kF64Rows + threadIdx.x;
+    const int row = bx * kF64Rows + threadIdx.x;
     const bool live = row < rows;
     const int s = live ? row / A.dx : 0, a = live ? row % A.dx : 0;
     const int32_t *pi = s > 0 ? A.perms + (size_t)(s - 1) * A.N : nullptr;
     const float *xcol = A.base + A.cols[a];
     const double mx = A.mean[a];
-    double acc[kGaussMaxDims];
+    double acc[DW4];
 #pragma unroll
-    for (int w = 0; w < kGaussMaxDims; ++w) acc[w] = 0.0;
+    for (int w = 0; w < DW4; ++w) acc[w] = 0.0;
     const int nchunks = (A.N + kGaussKC - 1) / kGaussKC;
-    const int c0 = blockIdx.y * A.chunks_per_split;
+    const int c0 = by * A.chunks_per_split;
     const int c1 = min(nchunks, c0 + A.chunks_per_split);
     for (int c = c0; c < c1; ++c) {
         const int t0 = c * kGaussKC, n = min(kGaussKC, A.N - t0);
         __syncthreads();
-        for (int e = threadIdx.x; e < n * dw; e += kF64Rows) {
-            const int t = e / dw, w = e - t * dw;
-            sW[t][w] = (double)A.base[A.cols[A.dx + w] + t0 + t] - A.mean[A.dx + w];
+        for (int e = threadIdx.x; e < kGaussKC * DW4; e += kF64Rows) {
+            const int t = e / DW4, w = e - t * DW4;
+            sW[t][w] = (t < n && w < dw)
+                           ? (double)A.base[A.cols[A.dx + w] + t0 + t] - A.mean[A.dx + w]
+                           : 0.0;
         }
         __syncthreads();
         if (!live) continue;
@@ -541,15 +546,30 @@ __global__ void __launch_bounds__(kF64Rows) gauss_cross_f64_kernel(GaussArgs A)
             const int src = pi ? pi[t0 + t] : t0 + t;
             const double xv = (double)xcol[src] - mx;
 #pragma unroll
-            for (int w = 0; w < kGaussMaxDims; ++w)
-                if (w < dw) acc[w] = fma(xv, sW[t][w], acc[w]);
+            for (int w = 0; w < DW4; ++w) acc[w] = fma(xv, sW[t][w], acc[w]);
         }
     }
     if (!live) return;
-    double *dst = A.cross_part + ((size_t)blockIdx.y * rows + row) * dw;
+    double *dst = A.cross_part + ((size_t)by * rows + row) * dw;
 #pragma unroll
-    for (int w = 0; w < kGaussMaxDims; ++w)
+    for (int w = 0; w < DW4; ++w)
         if (w < dw) dst[w] = acc[w];
+}
+
+__device__ __forceinline__ void gauss_cross_f64_any(const GaussArgs &A, int bx, int by)
+{
+    __shared__ double sW[kGaussKC][kGaussMaxDims];
+    switch ((A.dw + 3) >> 2) {
+    case 0:
+    case 1: gauss_cross_f64_body<4>(A, bx, by, sW); break;
+    case 2: gauss_cross_f64_body<8>(A, bx, by, sW); break;
+    case 3: gauss_cross_f64_body<12>(A, bx, by, sW); break;
+    case 4: gauss_cross_f64_body<16>(A, bx, by, sW); break;
+    case 5: gauss_cross_f64_body<20>(A, bx, by, sW); break;
+    case 6: gauss_cross_f64_body<24>(A, bx, by, sW); break;
+    case 7: gauss_cross_f64_body<28>(A, bx, by, sW); break;
+    default: gauss_cross_f64_body<32>(A, bx, by, sW); break;
+    }
 }
 
 // Order-preserving integer image of the estimates, in the (hi, lo) int128 form
@@ -568,7 +588,79 @@ __global__ void gauss_keys_kernel(const double *v, int n, long long *keys, int *
     keys[2 * (size_t)i + 1] = k;
 }
 
+__global__ void gauss_mean_kernel(GaussArgs A) { gauss_mean_body(A, blockIdx.x); }
+__global__ void gauss_cov_kernel(GaussArgs A) { gauss_cov_body(A, blockIdx.x); }
+__global__ void gauss_factor_kernel(GaussArgs A) { gauss_factor_body(A); }
+__global__ void gauss_schur_kernel(GaussArgs A, double gamma)
+{
+    gauss_schur_body(A, gamma, blockIdx.x * blockDim.x + threadIdx.x);
+}
+__global__ void gauss_cross_reduce_kernel(GaussArgs A)
+{
+    gauss_cross_reduce_body(A, blockIdx.x * (long long)blockDim.x + threadIdx.x);
+}
+
+// The same kernels over a batch of estimates: estimate blockIdx.z, its
+// arguments read from args; blocks beyond the estimate's own grid return.
+__global__ void gauss_mean_batch(const GaussArgs *args)
+{
+    const GaussArgs A = args[blockIdx.z];
+    if ((int)blockIdx.x < A.d) gauss_mean_body(A, blockIdx.x);
+}
+__global__ void gauss_cov_batch(const GaussArgs *args)
+{
+    const GaussArgs A = args[blockIdx.z];
+    if ((int)blockIdx.x < A.d * (A.d + 1) / 2) gauss_cov_body(A, blockIdx.x);
+}
+__global__ void gauss_factor_batch(const GaussArgs *args)
+{
+    const GaussArgs A = args[blockIdx.z];
+    gauss_factor_body(A);
+}
+__global__ void __launch_bounds__(kF64Rows) gauss_cross_f64_batch(const GaussArgs *args)
+{
+    const GaussArgs A = args[blockIdx.z];
+    if ((int)blockIdx.x * kF64Rows < (A.S + 1) * A.dx && (int)blockIdx.y < A.splits)
+        gauss_cross_f64_any(A, blockIdx.x, blockIdx.y);
+}
+__global__ void gauss_cross_reduce_batch(const GaussArgs *args)
+{
+    const GaussArgs A = args[blockIdx.z];
+    gauss_cross_reduce_body(A, blockIdx.x * (long long)blockDim.x + threadIdx.x);
+}
+__global__ void gauss_schur_f64_batch(const GaussArgs *args)
+{
+    const GaussArgs A = args[blockIdx.z];
+    gauss_schur_body(A, gauss_f64_gamma(A.N), blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 }  // namespace
+
+cudaError_t gauss_launch_batch_f64(const GaussArgs *args_dev, const GaussArgs *args_host, int n,
+                                   cudaStream_t st)
+{
+    if (n < 1) return cudaSuccess;
+    if (n > 65535) return cudaErrorInvalidValue;
+    int md = 1, mrb = 1, msp = 1, ms = 1;
+    long long mtot = 1;
+    for (int i = 0; i < n; ++i) {
+        const GaussArgs &A = args_host[i];
+        const int rows = (A.S + 1) * A.dx;
+        if (A.splits < 1 || A.splits > 65535) return cudaErrorInvalidValue;
+        md = std::max(md, A.d);
+        mrb = std::max(mrb, (rows + kF64Rows - 1) / kF64Rows);
+        msp = std::max(msp, A.splits);
+        ms = std::max(ms, A.S + 1);
+        mtot = std::max(mtot, (long long)rows * A.dw);
+    }
+    gauss_mean_batch<<<dim3(md, 1, n), 256, 0, st>>>(args_dev);
+    gauss_cov_batch<<<dim3(md * (md + 1) / 2, 1, n), 256, 0, st>>>(args_dev);
+    gauss_factor_batch<<<dim3(1, 1, n), 32, 0, st>>>(args_dev);
+    gauss_cross_f64_batch<<<dim3(mrb, msp, n), kF64Rows, 0, st>>>(args_dev);
+    gauss_cross_reduce_batch<<<dim3((unsigned)((mtot + 255) / 256), 1, n), 256, 0, st>>>(args_dev);
+    gauss_schur_f64_batch<<<dim3((ms + 63) / 64, 1, n), 64, 0, st>>>(args_dev);
+    return cudaGetLastError();
+}
 
 cudaError_t gauss_launch_keys(const double *v, int n, long long *keys, int *bad, cudaStream_t st)
 {
@@ -608,27 +700,6 @@ cudaError_t gauss_launch_cross_tc(const GaussArgs &A, cudaStream_t st)
     const long long total = (long long)rows * A.dw;
     gauss_cross_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(A);
     return cudaGetLastError();
-}
-
-cudaError_t gauss_launch_cross_f64(const GaussArgs &A, cudaStream_t st)
-{
-    const int rows = (A.S + 1) * A.dx;
-    if (A.splits < 1 || A.splits > 65535) return cudaErrorInvalidValue;
-    gauss_cross_f64_kernel<<<dim3((rows + kF64Rows - 1) / kF64Rows, A.splits), kF64Rows, 0, st>>>(
-        A);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const long long total = (long long)rows * A.dw;
-    gauss_cross_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(A);
-    return cudaGetLastError();
-}
-
-double gauss_f64_gamma(int N)
-{
-    // a sum of N FP64 products, |error| <= gamma_N sum |x||w| with
-    // gamma_N = N u / (1 - N u), u = 2^-53, plus the centring roundings
-    const double nu = (double)(N + 2) * std::ldexp(1.0, -53);
-    return nu / (1.0 - nu);
 }
 
 double gauss_tc_gamma()

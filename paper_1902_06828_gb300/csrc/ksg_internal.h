@@ -169,8 +169,8 @@ cudaError_t launch_perms_trials(int32_t *out, int R, int n, uint64_t seed, uint6
 // and owns launch CTAs perm_begin .. perm_begin + n_perm - 1.
 struct PermJob {
     int32_t *out;
-    int n, n_perm, s_first;
-    uint64_t seed, target, stage, iter;
+    int n, n_perm;
+    uint64_t s_first, seed, target, stage, iter;
     long long perm_begin;
 };
 cudaError_t launch_perms_multi(const PermJob *jobs, int n_jobs, long long total, int max_n,

@@ -1488,7 +1488,7 @@ __global__ void fisher_yates_multi_kernel(const PermJob *jobs, int n_jobs, int s
     h0 = sm64_once(h0 ^ J.iter);
     if (in_smem && n <= 65535) {
         uint16_t *p16 = reinterpret_cast<uint16_t *>(sperm);
-        fy_shuffle16(p16, p16 + n, n, sm64_once(h0 ^ (uint64_t)(J.s_first + r)), dst);
+        fy_shuffle16(p16, p16 + n, n, sm64_once(h0 ^ (J.s_first + (uint64_t)r)), dst);
         return;
     }
     int32_t *p = in_smem ? sperm : dst;
@@ -1499,7 +1499,7 @@ __global__ void fisher_yates_multi_kernel(const PermJob *jobs, int n_jobs, int s
     uint64_t h = sm64_once(J.seed ^ J.target);
     h = sm64_once(h ^ J.stage);
     h = sm64_once(h ^ J.iter);
-    fy_shuffle(p, n, sm64_once(h ^ (uint64_t)(J.s_first + r)), jb);
+    fy_shuffle(p, n, sm64_once(h ^ (J.s_first + (uint64_t)r)), jb);
     if (in_smem)
         for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = sperm[i];
 }

@@ -16,11 +16,14 @@ using namespace teksg;
 
 namespace {
 
-// Shape of one estimate (N points, S surrogates, X / Y / Z dimensions) and the
-// number of doubles of its workspace: means, covariance, the two Cholesky
-// factors, their inverse norms, scratch, the cross-covariances and their
-// per-split partial sums.  The estimates and error bounds are bound elsewhere.
-size_t gauss_shape(GaussArgs &A, int N, int S, int dx, int dy, int dz)
+constexpr int kGaussBatch = 4096;   // estimates per batched launch (grid z)
+
+// Shape of one estimate (N points, S surrogates, X / Y / Z dimensions, the
+// points split `splits` ways for the contraction) and the number of doubles
+// of its workspace: means, covariance, the two Cholesky factors, their
+// inverse norms, scratch, the cross-covariances and their per-split partial
+// sums.  The estimates and error bounds are bound elsewhere.
+size_t gauss_shape(GaussArgs &A, int N, int S, int dx, int dy, int dz, int splits)
 {
     A.N = N;
     A.S = S;
@@ -29,7 +32,7 @@ size_t gauss_shape(GaussArgs &A, int N, int S, int dx, int dy, int dz)
     A.dw = dy + dz;
     A.d = dx + dy + dz;
     const int nchunks = (N + 31) / 32;
-    const int splits = gauss_cross_splits((S + 1) * dx, N);
+    splits = std::max(1, std::min(splits, nchunks));
     A.chunks_per_split = (nchunks + splits - 1) / splits;
     A.splits = (nchunks + A.chunks_per_split - 1) / A.chunks_per_split;
     const size_t d = (size_t)A.d, dw = (size_t)A.dw;
@@ -78,18 +81,14 @@ te_status run_groups_gauss(te_ctx *ctx, const std::vector<HostGroup> &groups, in
     // differ only in the permutation.  Member s of a candidate writes slot
     // slot0 + s and, for s >= 1, reads permutation perms + (s - 1) N.  The
     // test decisions compare these estimates, so the cross-covariances are
-    // summed in FP64 (gauss_launch_cross_f64): decisions then agree with an
+    // summed in FP64 (gauss_launch_batch_f64): decisions then agree with an
     // FP64 evaluation except at ties closer than ~1e-12, where the split-TF32
-    // contraction of cmi_gauss (~1e-7) would flip near-ties.
-    struct Est {
-        const HostGroup *g;
-        int xc, S, slot0;
-        const int32_t *perms;
-        size_t col0;
-    };
-    std::vector<Est> est;
+    // contraction of cmi_gauss (~1e-7) would flip near-ties.  Estimates run in
+    // batches, one launch per kernel per batch; each has its own workspace.
+    std::vector<GaussArgs> est;
+    std::vector<int> slot0;
     std::vector<int> cols;
-    size_t ws = 0;
+    std::vector<size_t> col0;
     for (const HostGroup &g : groups) {
         const int N = g.data->T - g.max_lag;
         const int dy = (int)g.y.size(), dz = (int)g.z.size();
@@ -111,44 +110,74 @@ te_status run_groups_gauss(te_ctx *ctx, const std::vector<HostGroup> &groups, in
             if (!ok)
                 return fail(ctx, TE_EINTERNAL,
                             "Gaussian estimates need consecutive slots and permutations");
-            est.push_back(Est{&g, kv.first, S, ms[0]->out, p1, cols.size()});
+            GaussArgs A{};
+            A.N = N;
+            A.S = S;
+            A.dx = g.dx;
+            A.dy = dy;
+            A.d = g.dx + dy + dz;   // shape completed per batch
+            A.base = g.data->d_series;
+            A.perms = p1;
+            est.push_back(A);
+            slot0.push_back(ms[0]->out);
+            col0.push_back(cols.size());
             for (int a = 0; a < g.dx; ++a)
                 cols.push_back(gauss_col(g.data, g.max_lag, g.xvars[kv.first + a]));
             for (const te_var &v : g.y) cols.push_back(gauss_col(g.data, g.max_lag, v));
             for (const te_var &v : g.z) cols.push_back(gauss_col(g.data, g.max_lag, v));
-            GaussArgs A{};
-            ws = std::max(ws, gauss_shape(A, N, S, g.dx, dy, dz));
         }
     }
-    // doubles: shared per-estimate workspace, then estimates and bounds of all
-    // slots; ints: status flags, then the columns of every estimate
+    // shapes: a batch splits each estimate's points so that the contraction
+    // has about eight CTAs per SM in all
+    const int n_est = (int)est.size();
+    size_t ws = 0;
+    std::vector<size_t> off(n_est);
+    for (int b0 = 0; b0 < n_est; b0 += kGaussBatch) {
+        const int nb = std::min(kGaussBatch, n_est - b0);
+        size_t w = 0;
+        for (int i = b0; i < b0 + nb; ++i) {
+            GaussArgs &A = est[i];
+            const int blocks = ((A.S + 1) * A.dx + 127) / 128;
+            const int splits = (8 * 152 + nb * blocks - 1) / (nb * blocks);
+            off[i] = w;
+            w += gauss_shape(A, A.N, A.S, A.dx, A.dy, A.d - A.dx - A.dy, splits);
+        }
+        ws = std::max(ws, w);
+    }
+    // doubles: batch workspace, then estimates and bounds of all slots;
+    // then the batch's argument blocks; ints: status flags, the columns
     const size_t nd = ws + 2 * (size_t)n_out;
+    const size_t args_off = nd * 8;
+    const size_t int_off = args_off + (size_t)kGaussBatch * sizeof(GaussArgs);
     te_status st;
-    if ((st = ensure_dev(ctx, ctx->ws_gauss, nd * 8 + (2 + cols.size()) * 4))) return st;
+    if ((st = ensure_dev(ctx, ctx->ws_gauss, int_off + (2 + cols.size()) * 4))) return st;
     if ((st = ensure_dev(ctx, ctx->ws_keys, (size_t)std::max(n_out, 1) * 16))) return st;
-    double *w = (double *)ctx->ws_gauss.p;
+    char *base = (char *)ctx->ws_gauss.p;
+    double *w = (double *)base;
     double *v_out = w + ws, *v_err = v_out + n_out;
-    int *status = (int *)(w + nd), *cols_dev = status + 2;
+    GaussArgs *args_dev = (GaussArgs *)(base + args_off);
+    int *status = (int *)(base + int_off), *cols_dev = status + 2;
     CK(cudaMemsetAsync(status, 0, 2 * sizeof(int), ctx->stream), "cudaMemsetAsync");
     CK(cudaMemsetAsync(v_out, 0, (size_t)n_out * 8, ctx->stream), "cudaMemsetAsync");
     if (!cols.empty())
         CK(copy_h2d(ctx, cols_dev, cols.data(), cols.size() * 4), "cudaMemcpyAsync");
-    for (const Est &e : est) {
-        const HostGroup &g = *e.g;
-        GaussArgs A{};
-        gauss_shape(A, g.data->T - g.max_lag, e.S, g.dx, (int)g.y.size(), (int)g.z.size());
-        gauss_bind(A, w);
-        A.base = g.data->d_series;
-        A.cols = cols_dev + e.col0;
-        A.perms = e.perms;
+    for (int i = 0; i < n_est; ++i) {
+        GaussArgs &A = est[i];
+        gauss_bind(A, w + off[i]);
+        A.cols = cols_dev + col0[i];
         A.status = status;
-        A.out = v_out + e.slot0;
-        A.err = v_err + e.slot0;
-        CK(gauss_launch_stats(A, ctx->stream), "Gaussian statistics launch");
-        CK(gauss_launch_cross_f64(A, ctx->stream), "FP64 cross-covariance launch");
-        CK(gauss_launch_schur(A, gauss_f64_gamma(A.N), ctx->stream), "Schur launch");
+        A.out = v_out + slot0[i];
+        A.err = v_err + slot0[i];
+        ctx->stats.estimates += (uint64_t)A.S + 1;
+    }
+    for (int b0 = 0; b0 < n_est; b0 += kGaussBatch) {
+        const int nb = std::min(kGaussBatch, n_est - b0);
+        // the previous batch's kernels precede this copy on the stream
+        CK(copy_h2d(ctx, args_dev, est.data() + b0, (size_t)nb * sizeof(GaussArgs)),
+           "cudaMemcpyAsync");
+        CK(gauss_launch_batch_f64(args_dev, est.data() + b0, nb, ctx->stream),
+           "Gaussian batch launch");
         ctx->stats.launches += 6;
-        ctx->stats.estimates += (uint64_t)e.S + 1;
     }
     CK(gauss_launch_keys(v_out, n_out, (long long *)ctx->ws_keys.p, status, ctx->stream),
        "key launch");
@@ -182,7 +211,7 @@ extern "C" te_status cmi_gauss(te_ctx *ctx, const te_data *data, const te_var *x
         CK(cudaSetDevice(ctx->device), "cudaSetDevice");
         // workspace: the estimate's doubles, its estimates and bounds, then ints
         GaussArgs A{};
-        const size_t ws = gauss_shape(A, N, S, dx, dy, dz);
+        const size_t ws = gauss_shape(A, N, S, dx, dy, dz, gauss_cross_splits((S + 1) * dx, N));
         const size_t nd = ws + 2 * (size_t)(S + 1);
         if ((st = ensure_dev(ctx, ctx->ws_gauss, nd * 8 + (size_t)(d + 8) * 4))) return st;
         if ((st = ensure_dev(ctx, ctx->ws_perm, (size_t)std::max(S, 1) * N * 4))) return st;

@@ -14,9 +14,9 @@
 //
 // Targets are independent, so every round gathers the next request of every
 // unfinished target and evaluates all of them (candidates x surrogates x
-// targets) in one fused KSG launch per kernel class, one permutation launch per
-// request (per candidate with independent surrogates) and one statistics
-// launch; only a few integers per request come back to the host.  With the
+// targets) in one fused KSG launch per kernel class, one permutation launch for
+// all of the round's permutation sets (one set per request, or per candidate
+// with independent surrogates) and one statistics launch; only a few integers per request come back to the host.  With the
 // linear-Gaussian estimator each candidate's estimate and surrogates run
 // through cmi_gauss's kernels instead, and the statistics compare the
 // estimates' order-preserving integer images.
@@ -222,6 +222,8 @@ te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_para
             int32_t *perm = (int32_t *)ctx->ws_perm.p;
             std::vector<HostGroup> groups;
             std::vector<StatReq> reqs;
+            std::vector<PermJob> pj;   // every plain permutation set of the round
+            long long perm_total = 0;
             int n_out = 0, cnt_total = 0, orig_total = 0;
             for (size_t r = 0; r < active.size(); ++r) {
                 TargetState &t = ts[active[r]];
@@ -230,17 +232,27 @@ te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_para
                 const size_t n_sets = set_off[r + 1] - set_off[r];
                 for (size_t c = 0; c < n_sets; ++c) {
                     const uint64_t s1 = 1 + ((uint64_t)c << 32);
-                    if (pooled)
+                    if (pooled) {
                         CK(launch_perms_trials(pr + c * (size_t)S * N, data->n_rep,
                                                data->trial_len, P.seed, (uint64_t)t.target,
                                                (uint64_t)t.stage, (uint64_t)iter, s1, S,
                                                trial_mode, ctx->stream),
                            "permutation launch");
-                    else
-                        CK(launch_perms(pr + c * (size_t)S * N, N, N, P.seed, (uint64_t)t.target,
-                                        (uint64_t)t.stage, (uint64_t)iter, s1, S, ctx->stream),
-                           "permutation launch");
-                    ctx->stats.launches++;
+                        ctx->stats.launches++;
+                    } else {
+                        PermJob q{};
+                        q.out = pr + c * (size_t)S * N;
+                        q.n = N;
+                        q.n_perm = S;
+                        q.s_first = s1;
+                        q.seed = P.seed;
+                        q.target = (uint64_t)t.target;
+                        q.stage = (uint64_t)t.stage;
+                        q.iter = (uint64_t)iter;
+                        q.perm_begin = perm_total;
+                        perm_total += S;
+                        pj.push_back(q);
+                    }
                 }
                 const te_var ypres = tv(te_var{t.target, 0});
                 // candidate `c0 + c` of the test uses permutation set c0 + c when
@@ -305,6 +317,15 @@ te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_para
                 orig_total += t.n_cand;
                 reqs.push_back(StatReq{(long long)t.out_base, t.n_cand, S, t.mode, t.cnt_off,
                                        t.orig_off});
+            }
+            if (!pj.empty()) {   // one launch for the round's permutation sets
+                const size_t bytes = pj.size() * sizeof(PermJob);
+                if ((st = ensure_dev(ctx, ctx->ws_stat, bytes + 16))) return st;
+                CK(copy_h2d(ctx, ctx->ws_stat.p, pj.data(), bytes), "cudaMemcpyAsync");
+                CK(launch_perms_multi((const PermJob *)ctx->ws_stat.p, (int)pj.size(), perm_total,
+                                      N, ctx->stream),
+                   "permutation launch");
+                ctx->stats.launches++;
             }
             if ((st = gauss ? run_groups_gauss(ctx, groups, n_out)
                             : run_groups(ctx, groups, n_out)))
