@@ -341,6 +341,40 @@ def run_gauss(args):
     print(json.dumps(line), flush=True)
 
 
+def run_gauss_network(args):
+    """The workload's full greedy network inference with the linear-Gaussian
+    estimator (te_network_infer, estimator "gauss": FP64 contraction, every
+    round's estimates in one batched launch per kernel).  Each step is one
+    blocking network inference; the rate is estimates per wall second."""
+    import torch
+    import paper_1902_06828_gb300 as te
+    series, params, desc = _workload(args.workload, args.T, 1)
+    params = {k: v for k, v in params.items() if k != "k"}
+    ctx = te.Context(0)
+    data = te.te_data_create(ctx, series)
+    for _ in range(args.warmup):
+        te.te_network_infer(ctx, data, estimator="gauss", **params)
+    torch.cuda.synchronize()
+    st0 = ctx.stats()
+    n_est, secs = 0, []
+    for _ in range(args.steps):
+        t1 = time.perf_counter()
+        g = te.te_network_infer(ctx, data, estimator="gauss", **params)
+        secs.append(time.perf_counter() - t1)
+        n_est += g["n_estimates"]
+    st1 = ctx.stats()
+    line = {"metric": "linear-Gaussian CMI estimates/s incl. surrogates, network inference at "
+                      "T=%d" % args.T,
+            "value": n_est / sum(secs), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / args.steps,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc.replace("k=4, ", "") + ", Gaussian estimator",
+                       "estimates_per_step": n_est / args.steps},
+            "gpu_launches_per_step": (st1["launches"] - st0["launches"]) / args.steps,
+            "edges": int(g["adjacency"].sum())}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -392,6 +426,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=80)
     ap.add_argument("--gauss", action="store_true",
                     help="linear-Gaussian estimator path (cmi_gauss) instead of the KSG network")
+    ap.add_argument("--gauss-network", action="store_true",
+                    help="the workload's network inference with the linear-Gaussian estimator")
     ap.add_argument("--plain-calls", type=int, default=30,
                     help="one-call-per-estimate calls timed for the plain-path comparison")
     args = ap.parse_args()
@@ -401,6 +437,8 @@ def main():
         return
     if args.gauss:
         return run_gauss(args)
+    if args.gauss_network:
+        return run_gauss_network(args)
     if args.serve:
         run_serve(args)
         return

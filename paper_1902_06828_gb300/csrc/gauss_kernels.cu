@@ -244,8 +244,9 @@ __device__ __forceinline__ void gauss_schur_body(const GaussArgs &A, double gamm
 // ---------------- tensor-core cross-covariance (tcgen05, split TF32) ----------------
 // D[m][n] = sum_t A[m][t] B[n][t] with A[m][t] = x_i(pi_s(t)) - mean_i (row m =
 // (surrogate s, X dim i)) and B[n][t] = w_n(t) - mean_n (n < dw, zero above).
-// Each operand is split in two TF32 parts, a = a_hi + a_lo (centred in FP64,
-// a_hi = tf32(a), a_lo = tf32(a - a_hi)); the product is a_hi b_hi + a_hi b_lo +
+// Each operand is split in two TF32 parts, a = a_hi + a_lo (X centred in FP32
+// by its FP64 mean taken as a sum of two floats, W centred in FP64; a_hi =
+// tf32(a), a_lo = tf32(a - a_hi)); the product is a_hi b_hi + a_hi b_lo +
 // a_lo b_hi, three tcgen05.mma.kind::tf32 per K step, FP32 accumulation in
 // tensor memory.  Every kGaussGroup chunks of 32 points the 128 x 32 FP32
 // accumulator is read back (tcgen05.ld) and added to FP64 registers, which
@@ -351,7 +352,10 @@ __global__ void __launch_bounds__(128, 1) gauss_cross_tc_kernel(GaussArgs A)
     const int ms = mvalid ? m / A.dx : 0, mi = mvalid ? m % A.dx : 0;
     const int32_t *perm = (mvalid && ms > 0) ? A.perms + (size_t)(ms - 1) * A.N : nullptr;
     const float *cx = A.base + A.cols[mi];
+    // X is centred in FP32 by the FP64 mean as a sum of two floats: two
+    // roundings of 2^-24 relative per value, and no FP64 work per value
     const double mx = A.mean[mi];
+    const float mx_hi = (float)mx, mx_lo = (float)(mx - (double)mx_hi);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -405,9 +409,9 @@ __global__ void __launch_bounds__(128, 1) gauss_cross_tc_kernel(GaussArgs A)
                 for (int k = 0; k < 16; ++k) {
                     float hi = 0.f, lo = 0.f;
                     if (tx[k] >= 0) {
-                        const double v = (double)xv[k] - mx;
-                        hi = __uint_as_float(to_tf32((float)v));
-                        lo = __uint_as_float(to_tf32((float)(v - (double)hi)));
+                        const float v = __fsub_rn(__fsub_rn(xv[k], mx_hi), mx_lo);
+                        hi = __uint_as_float(to_tf32(v));
+                        lo = __uint_as_float(to_tf32(__fsub_rn(v, hi)));   // v - hi is exact
                     }
                     const uint32_t off = cm_offset(tid, h16 + k);
                     *reinterpret_cast<float *>(hb + off) = hi;
@@ -704,9 +708,11 @@ cudaError_t gauss_launch_cross_tc(const GaussArgs &A, cudaStream_t st)
 
 double gauss_tc_gamma()
 {
-    // split products: 3 * 2^-22 relative; FP32 accumulation of at most
-    // 3 * kGaussKC * kGaussGroup products per group, 2^-23 per addition
-    return 3.0 * std::ldexp(1.0, -22) + 3.0 * kGaussKC * kGaussGroup * std::ldexp(1.0, -23);
+    // split products: 3 * 2^-22 relative; FP32 centring of X: 2 * 2^-24;
+    // FP32 accumulation of at most 3 * kGaussKC * kGaussGroup products per
+    // group, 2^-23 per addition
+    return 3.0 * std::ldexp(1.0, -22) + 2.0 * std::ldexp(1.0, -24) +
+           3.0 * kGaussKC * kGaussGroup * std::ldexp(1.0, -23);
 }
 
 cudaError_t gauss_launch_schur(const GaussArgs &A, double gamma, cudaStream_t st)
