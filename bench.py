@@ -541,6 +541,16 @@ def main():
     traffic = TRAFFIC_PER_MEMBER_POINT * mp_per_launch if ksg_launches else None
     alg_bytes = (4.0 * n_pts + 16.0) * (n_est / world) / max(ksg_launches, 1)
     value = n_est / (ms / 1e3)
+    # measured ceiling of the counted instruction mix (te_alu_peak, after the
+    # timed region): the kNN-pass and count-pass patterns run from registers,
+    # weighted by this run's counted ops (pair_evals = e1 + e2 and
+    # ksg_ops = 3 e1 + 7 e2 give the two passes' shares)
+    p_knn = te.te_alu_peak(ctx, "knn") / 1e12
+    p_cnt = te.te_alu_peak(ctx, "count") / 1e12
+    p_add = te.te_alu_peak(ctx, "fadd") / 1e12
+    e2 = (ops - 3.0 * pair_evals) / 4.0
+    ops1, ops2 = 3.0 * (pair_evals - e2), 7.0 * e2
+    peak_mix = (ops1 + ops2) / (ops1 / p_knn + ops2 / p_cnt) if ops > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -561,6 +571,15 @@ def main():
                      "kernel": "ksg_lane_kernel", "kernel_ms_per_launch":
                      kernel_ms / max(ksg_launches, 1), "launches": ksg_launches,
                      "peak_note": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived)",
+                     "peak_measured_mix": peak_mix,
+                     "frac_of_measured_mix": (achieved / peak_mix) if achieved and peak_mix
+                     else None,
+                     "peak_measured": {"knn_pass_pattern": p_knn, "count_pass_pattern": p_cnt,
+                                       "fp32_add_issue": p_add,
+                                       "count_pass_share_of_ops": (ops2 / ops) if ops else None,
+                                       "note": "te_alu_peak: each pass's counted instruction "
+                                               "pattern from registers at full occupancy, this "
+                                               "run; the mix weights them by this run's ops"},
                      "work": "3 ops per executed kNN-pass member-pair, 7 per count-pass one",
                      "pair_evals_executed": pair_evals, "pair_evals_bruteforce": pair_evals_bf,
                      "pruned_fraction": (1.0 - pair_evals / pair_evals_bf) if pair_evals_bf

@@ -209,6 +209,21 @@ te_status cmi_gauss(te_ctx *ctx, const te_data *data, const te_var *x, int32_t d
  * Errors: TE_EINVAL (proc out of range, T < 2), TE_ENOMEM, TE_ECUDA. */
 te_status te_autocorr_decay(te_ctx *ctx, const te_data *data, int32_t proc, int32_t *out_tau);
 
+/* ---- measurement support -------------------------------------------------- */
+
+/* Measured rate of the KSG kernel's counted operations on this GPU, the
+ * denominator of that kernel's roofline (measurement support; the paper has no
+ * counterpart).  kind 0: the kNN-pass pattern, per member-pair a subtract, a
+ * max with d_YZ and one step of the eight-point minimum and threshold compare
+ * (3 counted operations); kind 1: the count-pass pattern, per member-pair a
+ * subtract, three compares and three predicated increments (7); kind 2: plain
+ * FP32 adds (the issue limit, 1 each).  Each probe runs from registers, with
+ * the kernel's per-lane shape (4 query points x 2 members x 8-point blocks), at
+ * full occupancy for at least 20 ms on the context's stream.  *out_ops_per_s =
+ * counted lane operations per second.  Blocks until measured.
+ * Errors: TE_EINVAL (kind, NULL), TE_ENOMEM, TE_ECUDA. */
+te_status te_alu_peak(te_ctx *ctx, int32_t kind, double *out_ops_per_s);
+
 /* ---- greedy network inference -------------------------------------------- */
 
 typedef struct {

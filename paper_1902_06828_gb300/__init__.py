@@ -348,6 +348,16 @@ def te_get_stats(ctx: Context) -> dict:
     return ctx.stats()
 
 
+def te_alu_peak(ctx: Context, kind: str) -> float:
+    """Measured rate (counted lane operations per second) of the KSG kernel's
+    instruction pattern: kind "knn" (3 per member-pair), "count" (7 per
+    member-pair) or "fadd" (plain FP32 adds, the issue limit)."""
+    out = C.c_double()
+    k = {"knn": 0, "count": 1, "fadd": 2}[kind]
+    _check(ctx._h, ctx._lib.te_alu_peak(ctx._h, k, C.byref(out)))
+    return float(out.value)
+
+
 def te_autocorr_decay(ctx: Context, data: Data, proc: int = -1) -> int:
     """Autocorrelation decay time of one process (or the largest over all
     with proc = -1): the Theiler-window heuristic."""

@@ -99,6 +99,7 @@ SIGNATURES = {
                                    C.POINTER(C.POINTER(NetworkResult))]),
     "te_network_result_free": (None, [C.POINTER(NetworkResult)]),
     "te_autocorr_decay": (C.c_int, [_P, _P, _I32, C.POINTER(C.c_int32)]),
+    "te_alu_peak": (C.c_int, [_P, _I32, C.POINTER(C.c_double)]),
     "te_data_create_trials": (C.c_int, [_P, _P, _I32, _I32, _I32, _I32, C.c_int, _P]),
     "te_get_stats": (C.c_int, [_P, C.POINTER(Stats)]),
     "te_serve_start": (C.c_int, [_P, C.POINTER(ServeConfig)]),
