@@ -24,6 +24,10 @@ CASES = [
     ("chain3", [(0, 1), (1, 1), (1, 2)], [(2, 0)], [(2, 1)], 2, 20),            # dx = 3
     ("var10", [(3, 2)], [(0, 0)], [(0, 1), (0, 2), (4, 1)], 5, 100),
     ("var10", [(9, 2)], [(0, 0), (1, 0)], [(0, 1)] + [(q, 1) for q in range(2, 9)], 5, 40),
+    # the limits: dx = 8 and 32 variables in all
+    ("var10", [(q, 1) for q in range(1, 9)], [(0, 0)],
+     [(0, l) for l in range(1, 6)] + [(q, l) for q in range(1, 9) for l in (2, 3)] + [(9, 1), (9, 2)],
+     5, 30),
 ]
 
 

@@ -96,6 +96,9 @@ CASES_SHAPES = [
     (333, 5, [(0, 1), (2, 1), (3, 2)], [(1, 0)], [(1, 1)], 4, 0),           # dx = 3
     (301, 5, [(0, 1), (2, 2)], [(1, 0), (4, 0)], [(1, 1)], 3, 1),           # dx = 2, dy = 2
     (150, 6, [(0, 1)], [(1, 0)], [(p, l) for p in range(1, 6) for l in (1, 2)], 4, 0),  # dz = 10
+    # the limits: 32 joint dimensions with the largest k, and k = 16 alone
+    (211, 9, [(0, 1)], [(1, 0)], [(p, l) for p in range(1, 9) for l in range(1, 5)][:30], 16, 0),
+    (260, 4, [(0, 1)], [(1, 0)], [(1, 1)], 16, 1),
 ]
 
 
@@ -271,6 +274,11 @@ def test_validation_errors(te, ctx):
         te.te_data_create(ctx, bad)
     with pytest.raises(te.TEError, match="TE_EINVAL"):
         te.te_network_infer(ctx, data, n_surr=10, alpha_max=0.05)   # S * alpha <= 1
+    # 33 joint dimensions, one more than the limit
+    wide = te.te_data_create(ctx, np.random.default_rng(1).normal(size=(9, 60)).astype(np.float32))
+    z31 = [(p, l) for p in range(1, 9) for l in range(1, 5)][:31]
+    with pytest.raises(te.TEError, match="TE_EINVAL"):
+        te.cmi_ksg(ctx, wide, [(0, 1)], [(1, 0)], z31, k=4, max_lag=4)
 
 
 def test_torch_device_tensor_input(te, ctx):
