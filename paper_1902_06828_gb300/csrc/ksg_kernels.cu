@@ -1270,28 +1270,74 @@ __device__ void fy_shuffle(int32_t *p, int n, uint64_t st, int32_t *jb)
     __syncthreads();
 }
 
-// The same shuffle for n <= 65535 with the permutation and the draws as
-// 16-bit values in shared memory (4 bytes per point: more CTAs per SM), the
-// result widened into out.  Called by the whole CTA.
-__device__ void fy_shuffle16(uint16_t *p, uint16_t *jb, int n, uint64_t st, int32_t *out)
+// The draw of position i (1 <= i < n): j = floor(r (i + 1) / 2^64) with r the
+// (n - 1 - i)-th output of SplitMix64 from state st, mix(st + (n - i) gamma).
+__device__ __forceinline__ int fy_draw(uint64_t st, int n, int i)
+{
+    uint64_t z = st + (uint64_t)(n - i) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (int)__umul64hi(z, (uint64_t)(i + 1));
+}
+
+// The same shuffle for n <= 65535 with the permutation as 16-bit values in
+// shared memory (2 bytes per point), the result widened into out.  Warp 0
+// runs the swaps in batches of 32 positions as fy_apply does, each lane
+// computing its own draw, one batch ahead; no draw is stored, so a CTA needs
+// only the permutation and one warp.  Called by the whole CTA.
+__device__ void fy_shuffle16(uint16_t *p, int n, uint64_t st, int32_t *out)
 {
     for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = (uint16_t)i;
-    for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
-        uint64_t z = st + (uint64_t)(n - i) * 0x9E3779B97F4A7C15ull;   // draw k = n-1-i
-        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-        z ^= z >> 31;
-        jb[i] = (uint16_t)__umul64hi(z, (uint64_t)(i + 1));
-    }
     __syncthreads();
-    fy_apply(p, jb, n);
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int hi = n - 1;
+        int jn = (hi >= 1 && hi - lane >= 1) ? fy_draw(st, n, hi - lane) : 0;
+        while (hi >= 1) {
+            const int lo = hi - 31 > 1 ? hi - 31 : 1;
+            const int i = hi - lane;
+            const bool valid = i >= lo;
+            const int j = valid ? jn : -1 - lane;   // invalid lanes: distinct dummies
+            // the next batch's draws, while this one is applied
+            const int hn = lo - 1, in = hn - lane;
+            jn = (hn >= 1 && in >= 1) ? fy_draw(st, n, in) : 0;
+            const unsigned same = __match_any_sync(0xffffffffu, j);
+            const bool ok = !valid || (j < lo && __popc(same) == 1);
+            if (__all_sync(0xffffffffu, ok)) {
+                uint16_t a = 0, b = 0;
+                if (valid) {
+                    a = p[i];
+                    b = p[j];
+                }
+                __syncwarp();
+                if (valid) {
+                    p[i] = b;
+                    p[j] = a;
+                }
+                __syncwarp();
+            } else {
+                for (int k = 0; k <= hi - lo; ++k) {   // in order: position hi - k
+                    const int jj = __shfl_sync(0xffffffffu, j, k);
+                    if (lane == 0) {
+                        const uint16_t t = p[hi - k];
+                        p[hi - k] = p[jj];
+                        p[jj] = t;
+                    }
+                }
+                __syncwarp();
+            }
+            hi = hn;
+        }
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = (int32_t)p[i];
 }
 
 // in_smem: bit 0 = the permutation is built in shared memory, bit 1 = the
-// draws are computed in parallel into shared memory after it, 4 = both as
-// 16-bit values (n <= 65535)
+// draws are computed in parallel into shared memory after it, 4 = the
+// permutation as 16-bit values with the draws computed by the swapping warp
+// (n <= 65535)
 __global__ void fisher_yates_kernel(int32_t *out, long long stride, int n, uint64_t seed,
                                     uint64_t target, uint64_t stage, uint64_t iter,
                                     uint64_t s_first, int in_smem)
@@ -1303,7 +1349,7 @@ __global__ void fisher_yates_kernel(int32_t *out, long long stride, int n, uint6
         h = sm64_once(h ^ stage);
         h = sm64_once(h ^ iter);
         uint16_t *p16 = reinterpret_cast<uint16_t *>(sperm);
-        fy_shuffle16(p16, p16 + n, n, sm64_once(h ^ s), out + (long long)blockIdx.x * stride);
+        fy_shuffle16(p16, n, sm64_once(h ^ s), out + (long long)blockIdx.x * stride);
         return;
     }
     int32_t *p = (in_smem & 1) ? sperm : out + (long long)blockIdx.x * stride;
@@ -1488,7 +1534,7 @@ __global__ void fisher_yates_multi_kernel(const PermJob *jobs, int n_jobs, int s
     h0 = sm64_once(h0 ^ J.iter);
     if (in_smem && n <= 65535) {
         uint16_t *p16 = reinterpret_cast<uint16_t *>(sperm);
-        fy_shuffle16(p16, p16 + n, n, sm64_once(h0 ^ (J.s_first + (uint64_t)r)), dst);
+        fy_shuffle16(p16, n, sm64_once(h0 ^ (J.s_first + (uint64_t)r)), dst);
         return;
     }
     int32_t *p = in_smem ? sperm : dst;
@@ -1757,9 +1803,11 @@ cudaError_t launch_perms(int32_t *out, long long stride, int n, uint64_t seed, u
     // permutation alone, else neither
     int mode = 0;
     size_t bytes = 0;
-    if (n <= 65535 && smem <= 200 * 1024) {
+    int threads = 256;
+    if (n <= 65535) {
         mode = 4;
-        bytes = smem;   // 2 + 2 bytes per point
+        bytes = (size_t)n * 2;   // the permutation alone, one warp per CTA
+        threads = 32;
     } else if (2 * smem <= 200 * 1024) {
         mode = 3;
         bytes = 2 * smem;
@@ -1767,8 +1815,8 @@ cudaError_t launch_perms(int32_t *out, long long stride, int n, uint64_t seed, u
         mode = 1;
         bytes = smem;
     }
-    fisher_yates_kernel<<<n_perm, 256, bytes, st>>>(out, stride, n, seed, target, stage, iter,
-                                                    s_first, mode);
+    fisher_yates_kernel<<<n_perm, threads, bytes, st>>>(out, stride, n, seed, target, stage,
+                                                        iter, s_first, mode);
     return cudaGetLastError();
 }
 
@@ -1870,10 +1918,16 @@ cudaError_t launch_perms_multi(const PermJob *jobs, int n_jobs, long long total,
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
+    if (max_n <= 65535) {
+        // every job shuffles in 16 bits (2 bytes per point), one warp per CTA
+        fisher_yates_multi_kernel<<<(unsigned)total, 32, (size_t)max_n * 2, st>>>(jobs, n_jobs,
+                                                                                 max_n, 0);
+        return cudaGetLastError();
+    }
     const int smem_n = max_n * 4 <= 200 * 1024 ? max_n : 0;
-    // n <= 65535 shuffles in 16 bits (4 bytes per point); larger ones keep
-    // their draws beside the permutation when that fits
-    const int jb_ok = smem_n > 0 && max_n > 65535 && (size_t)max_n * 8 <= 200 * 1024;
+    // larger permutations keep their draws beside the permutation when that
+    // fits; jobs of at most 65535 points still shuffle in 16 bits
+    const int jb_ok = smem_n > 0 && (size_t)max_n * 8 <= 200 * 1024;
     fisher_yates_multi_kernel<<<(unsigned)total, 256, (size_t)smem_n * (jb_ok ? 8 : 4), st>>>(
         jobs, n_jobs, smem_n, jb_ok);
     return cudaGetLastError();
