@@ -25,6 +25,7 @@ struct GaussArgs {
                             // [1] 1: a tensor-core wait timed out
     double *cross;          // [S + 1][dx][dw] cross-covariance of permuted X with W
     double *out, *err;      // [S + 1] estimates and error bounds
+    double *xc;             // [dx][N] X columns centred in FP64 (FP64 contraction only)
     // the contraction is split along the points: split p sums chunks
     // [p * chunks_per_split, ...) into cross_part[p][S + 1][dx][dw]
     int splits, chunks_per_split;
@@ -45,9 +46,10 @@ __host__ __device__ inline double gauss_f64_gamma(int N)
     const double nu = (double)(N + 2) * 0x1p-53;
     return nu / (1.0 - nu);
 }
-// the whole FP64 pipeline (means, covariance, factors, FP64 contraction and
-// its reduction, Schur complements) for n <= 65535 estimates in one launch
-// per kernel: estimate i's arguments at args_dev[i] (device) and args_host[i]
+// the whole FP64 pipeline (means, covariance, factors, centred X columns into
+// xc, FP64 contraction and its reduction, Schur complements) for n <= 65535
+// estimates in one launch per kernel: estimate i's arguments at args_dev[i]
+// (device) and args_host[i]
 cudaError_t gauss_launch_batch_f64(const GaussArgs *args_dev, const GaussArgs *args_host, int n,
                                    cudaStream_t st);
 cudaError_t gauss_launch_schur(const GaussArgs &A, double gamma, cudaStream_t st);

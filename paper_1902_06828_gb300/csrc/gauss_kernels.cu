@@ -161,24 +161,32 @@ __device__ double inv_frob2_warp(const double *L, int n, int ld, double (*col)[3
 // (never cleared here, so estimates sharing a status word accumulate it).
 __device__ __forceinline__ void gauss_factor_body(const GaussArgs &A)
 {
+    // the factorisations run in shared memory (a warp's dependent steps would
+    // otherwise wait on global memory) and the factors are written back
     __shared__ double col[32][33];
+    __shared__ double sW[kGaussMaxDims * kGaussMaxDims], sZ[kGaussMaxDims * kGaussMaxDims];
     if (threadIdx.x >= 32) return;
     const int lane = threadIdx.x;
     const int dx = A.dx, dw = A.dw, dy = A.dy, dz = dw - dy, d = A.d;
     for (int e = lane; e < dw * dw; e += 32) {
         const int r = e / dw, c = e % dw;
-        A.LW[r * dw + c] = c <= r ? A.cov[(dx + r) * d + dx + c] : 0.0;
-        if (r < dz && c < dz) A.LZ[r * dw + c] = c <= r ? A.cov[(dx + dy + r) * d + dx + dy + c] : 0.0;
+        sW[r * dw + c] = c <= r ? A.cov[(dx + r) * d + dx + c] : 0.0;
+        if (r < dz && c < dz) sZ[r * dw + c] = c <= r ? A.cov[(dx + dy + r) * d + dx + dy + c] : 0.0;
     }
     __syncwarp();
-    bool ok = chol_warp(A.LW, dw, dw);
-    if (dz > 0) ok = ok && chol_warp(A.LZ, dz, dw);
+    bool ok = chol_warp(sW, dw, dw);
+    if (dz > 0) ok = ok && chol_warp(sZ, dz, dw);
     if (lane == 0 && !ok) A.status[0] = 1;
     if (!ok) return;
     __syncwarp();
-    const double nw = inv_frob2_warp(A.LW, dw, dw, col);
+    for (int e = lane; e < dw * dw; e += 32) {
+        const int r = e / dw, c = e % dw;
+        A.LW[e] = sW[e];
+        if (r < dz && c < dz) A.LZ[e] = sZ[e];
+    }
+    const double nw = inv_frob2_warp(sW, dw, dw, col);
     __syncwarp();
-    const double nz = dz > 0 ? inv_frob2_warp(A.LZ, dz, dw, col) : 0.0;
+    const double nz = dz > 0 ? inv_frob2_warp(sZ, dz, dw, col) : 0.0;
     if (lane == 0) {
         A.norms[0] = nw;
         A.norms[1] = nz;
@@ -187,7 +195,11 @@ __device__ __forceinline__ void gauss_factor_body(const GaussArgs &A)
 
 // Per surrogate (one thread): Schur complements given Z and given W, their
 // log-determinants, the estimate and a first-order bound on its error from
-// the cross-covariance error model |dS_XW_ij| <= gamma sqrt(S_ii S_jj).
+// the cross-covariance error model |dS_XW_ij| <= gamma sqrt(S_ii S_jj), whose
+// squared Frobenius norm over (a, r) is gamma^2 tr(S_XX) sum_r S_rr.  One
+// thread per surrogate keeps every FP64 lane busy (a warp per surrogate was
+// measured slower: GB300's FP64 pipe is narrow, so idle lanes cost more than
+// the dependent chain).
 __device__ __forceinline__ void gauss_schur_body(const GaussArgs &A, double gamma, int s)
 {
     if (s > A.S) return;
@@ -195,6 +207,8 @@ __device__ __forceinline__ void gauss_schur_body(const GaussArgs &A, double gamm
     const double *c = A.cross + (size_t)s * dx * dw;   // [dx][dw]
     double v[kGaussMaxDims], Sm[kGaussMaxX * kGaussMaxX], tmp[kGaussMaxDims];
     double ld[2], bound[2];
+    double sxx = 0.0;
+    for (int a = 0; a < dx; ++a) sxx += A.cov[a * d + a];
     for (int which = 0; which < 2; ++which) {
         // which 0: given Z (trailing dz entries of W); 1: given W
         const int n = which == 0 ? dz : dw;
@@ -203,20 +217,19 @@ __device__ __forceinline__ void gauss_schur_body(const GaussArgs &A, double gamm
         // Sm = S_XX - V^T V, V = L^-1 C_V  (column per x dim)
         for (int a = 0; a < dx; ++a)
             for (int b = 0; b < dx; ++b) Sm[a * dx + b] = A.cov[a * d + b];
-        double vnorm2 = 0.0, dcnorm2 = 0.0;
+        double vnorm2 = 0.0, svv = 0.0;
         double vall[kGaussMaxX * kGaussMaxDims];
+        for (int r = 0; r < n; ++r) svv += A.cov[(dx + off + r) * d + dx + off + r];
         for (int a = 0; a < dx; ++a) {
             for (int r = 0; r < n; ++r) {
                 double t = c[a * dw + off + r];
                 for (int k = 0; k < r; ++k) t -= L[r * dw + k] * v[k];
                 v[r] = t / L[r * dw + r];
                 vnorm2 += v[r] * v[r];
-                const double e = gamma * sqrt(A.cov[a * d + a] *
-                                              A.cov[(dx + off + r) * d + dx + off + r]);
-                dcnorm2 += e * e;
             }
             for (int r = 0; r < n; ++r) vall[a * kGaussMaxDims + r] = v[r];
         }
+        const double dcnorm2 = gamma * gamma * sxx * svv;
         for (int a = 0; a < dx; ++a)
             for (int b = 0; b < dx; ++b) {
                 double t = 0.0;
@@ -514,9 +527,11 @@ __device__ __forceinline__ void gauss_cross_reduce_body(const GaussArgs &A, long
 // points are split into A.splits ranges of chunks_per_split chunks (grid y),
 // and the tensor-core kernel's reduction adds the splits in order.
 constexpr int kF64Rows = 128;
-// DW4 = dw rounded up to a multiple of 4: the W values past dw are staged as
+// DW4 = dw rounded up to a multiple of 2: the W values past dw are staged as
 // zeros, so the inner loop has no per-column guard (a guarded loop unrolled to
 // the 32-column maximum would issue 32 FP64 FMAs per point whatever dw is).
+// The X values are gathered already centred (gauss_centre_batch), so a point
+// costs one FP64 FMA per column and nothing else on the FP64 pipe.
 template <int DW4>
 __device__ __forceinline__ void gauss_cross_f64_body(const GaussArgs &A, int bx, int by,
                                                      double (*sW)[kGaussMaxDims])
@@ -526,8 +541,7 @@ __device__ __forceinline__ void gauss_cross_f64_body(const GaussArgs &A, int bx,
     const bool live = row < rows;
     const int s = live ? row / A.dx : 0, a = live ? row % A.dx : 0;
     const int32_t *pi = s > 0 ? A.perms + (size_t)(s - 1) * A.N : nullptr;
-    const float *xcol = A.base + A.cols[a];
-    const double mx = A.mean[a];
+    const double *xcol = A.xc + (size_t)a * A.N;
     double acc[DW4];
 #pragma unroll
     for (int w = 0; w < DW4; ++w) acc[w] = 0.0;
@@ -548,7 +562,7 @@ __device__ __forceinline__ void gauss_cross_f64_body(const GaussArgs &A, int bx,
 #pragma unroll 4
         for (int t = 0; t < n; ++t) {
             const int src = pi ? pi[t0 + t] : t0 + t;
-            const double xv = (double)xcol[src] - mx;
+            const double xv = xcol[src];
 #pragma unroll
             for (int w = 0; w < DW4; ++w) acc[w] = fma(xv, sW[t][w], acc[w]);
         }
@@ -563,15 +577,23 @@ __device__ __forceinline__ void gauss_cross_f64_body(const GaussArgs &A, int bx,
 __device__ __forceinline__ void gauss_cross_f64_any(const GaussArgs &A, int bx, int by)
 {
     __shared__ double sW[kGaussKC][kGaussMaxDims];
-    switch ((A.dw + 3) >> 2) {
+    switch ((A.dw + 1) >> 1) {
     case 0:
-    case 1: gauss_cross_f64_body<4>(A, bx, by, sW); break;
-    case 2: gauss_cross_f64_body<8>(A, bx, by, sW); break;
-    case 3: gauss_cross_f64_body<12>(A, bx, by, sW); break;
-    case 4: gauss_cross_f64_body<16>(A, bx, by, sW); break;
-    case 5: gauss_cross_f64_body<20>(A, bx, by, sW); break;
-    case 6: gauss_cross_f64_body<24>(A, bx, by, sW); break;
-    case 7: gauss_cross_f64_body<28>(A, bx, by, sW); break;
+    case 1: gauss_cross_f64_body<2>(A, bx, by, sW); break;
+    case 2: gauss_cross_f64_body<4>(A, bx, by, sW); break;
+    case 3: gauss_cross_f64_body<6>(A, bx, by, sW); break;
+    case 4: gauss_cross_f64_body<8>(A, bx, by, sW); break;
+    case 5: gauss_cross_f64_body<10>(A, bx, by, sW); break;
+    case 6: gauss_cross_f64_body<12>(A, bx, by, sW); break;
+    case 7: gauss_cross_f64_body<14>(A, bx, by, sW); break;
+    case 8: gauss_cross_f64_body<16>(A, bx, by, sW); break;
+    case 9: gauss_cross_f64_body<18>(A, bx, by, sW); break;
+    case 10: gauss_cross_f64_body<20>(A, bx, by, sW); break;
+    case 11: gauss_cross_f64_body<22>(A, bx, by, sW); break;
+    case 12: gauss_cross_f64_body<24>(A, bx, by, sW); break;
+    case 13: gauss_cross_f64_body<26>(A, bx, by, sW); break;
+    case 14: gauss_cross_f64_body<28>(A, bx, by, sW); break;
+    case 15: gauss_cross_f64_body<30>(A, bx, by, sW); break;
     default: gauss_cross_f64_body<32>(A, bx, by, sW); break;
     }
 }
@@ -611,6 +633,18 @@ __global__ void gauss_mean_batch(const GaussArgs *args)
     const GaussArgs A = args[blockIdx.z];
     if ((int)blockIdx.x < A.d) gauss_mean_body(A, blockIdx.x);
 }
+// xc[a][t] = x_a(t) - mean_a in FP64, grid y = X dim a
+__global__ void gauss_centre_batch(const GaussArgs *args)
+{
+    const GaussArgs A = args[blockIdx.z];
+    const int a = blockIdx.y;
+    if (a >= A.dx) return;
+    const float *col = A.base + A.cols[a];
+    const double m = A.mean[a];
+    double *dst = A.xc + (size_t)a * A.N;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < A.N; t += gridDim.x * blockDim.x)
+        dst[t] = (double)col[t] - m;
+}
 __global__ void gauss_cov_batch(const GaussArgs *args)
 {
     const GaussArgs A = args[blockIdx.z];
@@ -645,13 +679,14 @@ cudaError_t gauss_launch_batch_f64(const GaussArgs *args_dev, const GaussArgs *a
 {
     if (n < 1) return cudaSuccess;
     if (n > 65535) return cudaErrorInvalidValue;
-    int md = 1, mrb = 1, msp = 1, ms = 1;
+    int md = 1, mrb = 1, msp = 1, ms = 1, mdx = 1;
     long long mtot = 1;
     for (int i = 0; i < n; ++i) {
         const GaussArgs &A = args_host[i];
         const int rows = (A.S + 1) * A.dx;
         if (A.splits < 1 || A.splits > 65535) return cudaErrorInvalidValue;
         md = std::max(md, A.d);
+        mdx = std::max(mdx, A.dx);
         mrb = std::max(mrb, (rows + kF64Rows - 1) / kF64Rows);
         msp = std::max(msp, A.splits);
         ms = std::max(ms, A.S + 1);
@@ -660,6 +695,7 @@ cudaError_t gauss_launch_batch_f64(const GaussArgs *args_dev, const GaussArgs *a
     gauss_mean_batch<<<dim3(md, 1, n), 256, 0, st>>>(args_dev);
     gauss_cov_batch<<<dim3(md * (md + 1) / 2, 1, n), 256, 0, st>>>(args_dev);
     gauss_factor_batch<<<dim3(1, 1, n), 32, 0, st>>>(args_dev);
+    gauss_centre_batch<<<dim3(8, mdx, n), 256, 0, st>>>(args_dev);
     gauss_cross_f64_batch<<<dim3(mrb, msp, n), kF64Rows, 0, st>>>(args_dev);
     gauss_cross_reduce_batch<<<dim3((unsigned)((mtot + 255) / 256), 1, n), 256, 0, st>>>(args_dev);
     gauss_schur_f64_batch<<<dim3((ms + 63) / 64, 1, n), 64, 0, st>>>(args_dev);

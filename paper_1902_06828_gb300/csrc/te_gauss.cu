@@ -22,8 +22,10 @@ constexpr int kGaussBatch = 4096;   // estimates per batched launch (grid z)
 // points split `splits` ways for the contraction) and the number of doubles
 // of its workspace: means, covariance, the two Cholesky factors, their
 // inverse norms, scratch, the cross-covariances and their per-split partial
-// sums.  The estimates and error bounds are bound elsewhere.
-size_t gauss_shape(GaussArgs &A, int N, int S, int dx, int dy, int dz, int splits)
+// sums, and with xc the centred X columns.  The estimates and error bounds
+// are bound elsewhere.
+size_t gauss_shape(GaussArgs &A, int N, int S, int dx, int dy, int dz, int splits,
+                   bool xc = false)
 {
     A.N = N;
     A.S = S;
@@ -37,11 +39,11 @@ size_t gauss_shape(GaussArgs &A, int N, int S, int dx, int dy, int dz, int split
     A.splits = (nchunks + A.chunks_per_split - 1) / A.chunks_per_split;
     const size_t d = (size_t)A.d, dw = (size_t)A.dw;
     return d + d * d + 2 * dw * dw + 2 + kGaussMaxDims +
-           (size_t)(S + 1) * dx * dw * (1 + (size_t)A.splits);
+           (size_t)(S + 1) * dx * dw * (1 + (size_t)A.splits) + (xc ? (size_t)dx * N : 0);
 }
 
-// workspace pointers of a shaped estimate, starting at w
-void gauss_bind(GaussArgs &A, double *w)
+// workspace pointers of a shaped estimate, starting at w (xc: as shaped)
+void gauss_bind(GaussArgs &A, double *w, bool xc = false)
 {
     const size_t d = (size_t)A.d, dw = (size_t)A.dw;
     A.mean = w;
@@ -52,6 +54,7 @@ void gauss_bind(GaussArgs &A, double *w)
     A.scratch = A.norms + 2;
     A.cross = A.scratch + kGaussMaxDims;
     A.cross_part = A.cross + (size_t)(A.S + 1) * A.dx * dw;
+    A.xc = xc ? A.cross_part + (size_t)A.splits * (A.S + 1) * A.dx * dw : nullptr;
 }
 
 // offset of variable v's column at the first point: the value at point t is
@@ -140,7 +143,7 @@ te_status run_groups_gauss(te_ctx *ctx, const std::vector<HostGroup> &groups, in
             const int blocks = ((A.S + 1) * A.dx + 127) / 128;
             const int splits = (8 * 152 + nb * blocks - 1) / (nb * blocks);
             off[i] = w;
-            w += gauss_shape(A, A.N, A.S, A.dx, A.dy, A.d - A.dx - A.dy, splits);
+            w += gauss_shape(A, A.N, A.S, A.dx, A.dy, A.d - A.dx - A.dy, splits, true);
         }
         ws = std::max(ws, w);
     }
@@ -163,7 +166,7 @@ te_status run_groups_gauss(te_ctx *ctx, const std::vector<HostGroup> &groups, in
         CK(copy_h2d(ctx, cols_dev, cols.data(), cols.size() * 4), "cudaMemcpyAsync");
     for (int i = 0; i < n_est; ++i) {
         GaussArgs &A = est[i];
-        gauss_bind(A, w + off[i]);
+        gauss_bind(A, w + off[i], true);
         A.cols = cols_dev + col0[i];
         A.status = status;
         A.out = v_out + slot0[i];
@@ -177,7 +180,7 @@ te_status run_groups_gauss(te_ctx *ctx, const std::vector<HostGroup> &groups, in
            "cudaMemcpyAsync");
         CK(gauss_launch_batch_f64(args_dev, est.data() + b0, nb, ctx->stream),
            "Gaussian batch launch");
-        ctx->stats.launches += 6;
+        ctx->stats.launches += 7;
     }
     CK(gauss_launch_keys(v_out, n_out, (long long *)ctx->ws_keys.p, status, ctx->stream),
        "key launch");
@@ -230,11 +233,19 @@ extern "C" te_status cmi_gauss(te_ctx *ctx, const te_data *data, const te_var *x
         for (int a = 0; a < dy; ++a) cols.push_back(gauss_col(data, p->max_lag, y[a]));
         for (int a = 0; a < dz; ++a) cols.push_back(gauss_col(data, p->max_lag, z[a]));
         CK(copy_h2d(ctx, cols_dev, cols.data(), cols.size() * 4), "cudaMemcpyAsync");
+        CK(cudaMemsetAsync(A.status, 0, 2 * sizeof(int), ctx->stream), "cudaMemsetAsync");
+        // the statistics (means, covariance, FP64 factors) do not depend on
+        // the permutations: they run on the auxiliary stream while the
+        // permutations are drawn, and the contraction waits for both
+        if ((st = ensure_aux(ctx))) return st;
+        CK(cudaEventRecord(ctx->ev_fork, ctx->stream), "cudaEventRecord");
+        CK(cudaStreamWaitEvent(ctx->aux_stream, ctx->ev_fork, 0), "cudaStreamWaitEvent");
+        CK(gauss_launch_stats(A, ctx->aux_stream), "Gaussian statistics launch");
+        CK(cudaEventRecord(ctx->ev_join, ctx->aux_stream), "cudaEventRecord");
         CK(launch_perms((int32_t *)ctx->ws_perm.p, N, N, p->seed, p->stream_tag, 0, 0, 1, S,
                         ctx->stream),
            "permutation launch");
-        CK(cudaMemsetAsync(A.status, 0, 2 * sizeof(int), ctx->stream), "cudaMemsetAsync");
-        CK(gauss_launch_stats(A, ctx->stream), "Gaussian statistics launch");
+        CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0), "cudaStreamWaitEvent");
         CK(gauss_launch_cross_tc(A, ctx->stream), "tensor-core cross-covariance launch");
         const double gamma = gauss_tc_gamma();
         CK(gauss_launch_schur(A, gamma, ctx->stream), "Schur launch");

@@ -76,6 +76,15 @@ te_status ensure_pin(te_ctx *ctx, size_t bytes)
     return TE_OK;
 }
 
+te_status ensure_aux(te_ctx *ctx)
+{
+    if (ctx->aux_stream) return TE_OK;
+    CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
+    CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming), "cudaEventCreate");
+    CK(cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    return TE_OK;
+}
+
 // ---- digamma fixed-point table, double-double arithmetic ----------------
 // psi(1) = -gamma and psi(n + 1) = psi(n) + 1/n, carried as an unevaluated sum
 // hi + lo of two doubles (error-free two-sum; 1/n split with an exact FMA
@@ -755,6 +764,7 @@ void te_ctx_destroy(te_ctx *ctx)
     te_serve_stop(ctx);
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->aux_stream) cudaStreamSynchronize(ctx->aux_stream);
     DevBuf *bufs[] = {&ctx->ws_groups, &ctx->ws_members, &ctx->ws_cols,  &ctx->ws_acc,
                       &ctx->ws_keys,   &ctx->ws_perm,    &ctx->ws_stat,  &ctx->ws_dbg,
                       &ctx->ws_order,  &ctx->ws_ojobs,  &ctx->ws_cperm, &ctx->ws_gauss,
@@ -767,6 +777,9 @@ void te_ctx_destroy(te_ctx *ctx)
     if (ctx->work_host) cudaFreeHost(ctx->work_host);
     if (ctx->ev_a) cudaEventDestroy(ctx->ev_a);
     if (ctx->ev_b) cudaEventDestroy(ctx->ev_b);
+    if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
 }

@@ -79,6 +79,10 @@ struct te_ctx {
     unsigned long long *work_dev = nullptr;   // KSG kernel work counters [2], error flag [1]
     unsigned long long *work_host = nullptr;  // pinned copy
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    // second stream for work that overlaps the context's stream (created on
+    // first use) and the events that fork to it and join back
+    cudaStream_t aux_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int prepared = 0;
 };
 
@@ -98,6 +102,7 @@ te_status cuda_fail(te_ctx *ctx, cudaError_t e, const char *what);
 
 te_status ensure_dev(te_ctx *ctx, DevBuf &b, size_t bytes);
 te_status ensure_pin(te_ctx *ctx, size_t bytes);
+te_status ensure_aux(te_ctx *ctx);   // ctx->aux_stream, ev_fork, ev_join
 te_status ensure_q(te_ctx *ctx, int n_needed);   // Q[0..n_needed] on the device
 // Q[0..n_max] into a caller buffer (host), same arithmetic as ensure_q
 void digamma_q_fill(int n_max, int64_t *q);
