@@ -1283,51 +1283,59 @@ __device__ __forceinline__ int fy_draw(uint64_t st, int n, int i)
 
 // The same shuffle for n <= 65535 with the permutation as 16-bit values in
 // shared memory (2 bytes per point), the result widened into out.  Warp 0
-// runs the swaps in batches of 32 positions as fy_apply does, each lane
-// computing its own draw, one batch ahead; no draw is stored, so a CTA needs
-// only the permutation and one warp.  Called by the whole CTA.
+// walks the steps i = n-1 down to 1 in windows of 32, lane l holding step
+// hi - l and its draw j.  Each round applies at once the longest leading run
+// of steps whose swaps touch pairwise distinct positions: a step with j != i
+// allows runs of at most hi - j steps (its j must lie below the run), and a
+// draw repeated from an earlier step ends the run before it; disjoint swaps
+// commute, so the result equals the sequential loop exactly.  The next
+// window's draws come from this window's (shifted) and from draws computed
+// one window ahead.  No draw is stored, so a CTA needs only the permutation
+// and one warp.  Called by the whole CTA.
 __device__ void fy_shuffle16(uint16_t *p, int n, uint64_t st, int32_t *out)
 {
     for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = (uint16_t)i;
     __syncthreads();
     if (threadIdx.x < 32) {
+        const unsigned full = 0xffffffffu;
         const int lane = threadIdx.x;
+        const unsigned lower = (1u << lane) - 1u;
         int hi = n - 1;
-        int jn = (hi >= 1 && hi - lane >= 1) ? fy_draw(st, n, hi - lane) : 0;
+        int jc = (hi - lane >= 1) ? fy_draw(st, n, hi - lane) : 0;
         while (hi >= 1) {
-            const int lo = hi - 31 > 1 ? hi - 31 : 1;
             const int i = hi - lane;
-            const bool valid = i >= lo;
-            const int j = valid ? jn : -1 - lane;   // invalid lanes: distinct dummies
-            // the next batch's draws, while this one is applied
-            const int hn = lo - 1, in = hn - lane;
-            jn = (hn >= 1 && in >= 1) ? fy_draw(st, n, in) : 0;
-            const unsigned same = __match_any_sync(0xffffffffu, j);
-            const bool ok = !valid || (j < lo && __popc(same) == 1);
-            if (__all_sync(0xffffffffu, ok)) {
-                uint16_t a = 0, b = 0;
-                if (valid) {
-                    a = p[i];
-                    b = p[j];
-                }
-                __syncwarp();
-                if (valid) {
-                    p[i] = b;
-                    p[j] = a;
-                }
-                __syncwarp();
-            } else {
-                for (int k = 0; k <= hi - lo; ++k) {   // in order: position hi - k
-                    const int jj = __shfl_sync(0xffffffffu, j, k);
-                    if (lane == 0) {
-                        const uint16_t t = p[hi - k];
-                        p[hi - k] = p[jj];
-                        p[jj] = t;
-                    }
-                }
-                __syncwarp();
+            const bool valid = i >= 1;
+            const int j = valid ? jc : -1 - lane;   // invalid lanes: distinct dummies
+            // the window below, in case the whole window applies
+            const int is = hi - 32 - lane;
+            const int js = is >= 1 ? fy_draw(st, n, is) : 0;
+            int lim = !valid ? 0 : (j == i ? 32 : hi - j);
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {   // running minimum over lanes 0..lane
+                const int t = __shfl_up_sync(full, lim, o);
+                if (lane >= o) lim = min(lim, t);
             }
-            hi = hn;
+            const unsigned same = __match_any_sync(full, j);
+            const unsigned run = __ballot_sync(full, valid && lane < lim && (same & lower) == 0);
+            const int k = run == full ? 32 : __ffs(~run) - 1;   // >= 1: step hi always applies
+            const bool act = lane < k && j != i;
+            uint16_t a = 0, b = 0;
+            if (act) {
+                a = p[i];
+                b = p[j];
+            }
+            __syncwarp();
+            if (act) {
+                p[i] = b;
+                p[j] = a;
+            }
+            __syncwarp();
+            // next window hi - k: lane l < 32 - k takes lane l + k's draw, the
+            // others the draws computed ahead for lane l + k - 32
+            const int from_cur = __shfl_down_sync(full, j, k & 31);
+            const int from_ahead = __shfl_sync(full, js, (lane + k - 32) & 31);
+            jc = lane < 32 - k ? from_cur : from_ahead;
+            hi -= k;
         }
     }
     __syncthreads();
