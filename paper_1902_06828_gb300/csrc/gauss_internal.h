@@ -25,7 +25,8 @@ struct GaussArgs {
                             // [1] 1: a tensor-core wait timed out
     double *cross;          // [S + 1][dx][dw] cross-covariance of permuted X with W
     double *out, *err;      // [S + 1] estimates and error bounds
-    double *xc;             // [dx][N] X columns centred in FP64 (FP64 contraction only)
+    double *xc;             // [dx][N] X columns centred in FP64, stored as float pairs
+                            // (hi, lo) when dw <= kGaussFFMaxW (batched contraction only)
     // the contraction is split along the points: split p sums chunks
     // [p * chunks_per_split, ...) into cross_part[p][S + 1][dx][dw]
     int splits, chunks_per_split;
@@ -45,6 +46,14 @@ __host__ __device__ inline double gauss_f64_gamma(int N)
 {
     const double nu = (double)(N + 2) * 0x1p-53;
     return nu / (1.0 - nu);
+}
+// estimates with dw <= kGaussFFMaxW take the float-float contraction instead:
+// 3 * 2^-48 per product and at most 32^2 * 2^-48 per 32-point window (2^-37
+// covers both), then the FP64 sums
+constexpr int kGaussFFMaxW = 16;
+__host__ __device__ inline double gauss_batch_gamma(int N, int dw)
+{
+    return gauss_f64_gamma(N) + (dw <= kGaussFFMaxW ? 0x1p-37 : 0.0);
 }
 // the whole FP64 pipeline (means, covariance, factors, centred X columns into
 // xc, FP64 contraction and its reduction, Schur complements) for n <= 65535

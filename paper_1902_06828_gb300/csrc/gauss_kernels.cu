@@ -574,19 +574,106 @@ __device__ __forceinline__ void gauss_cross_f64_body(const GaussArgs &A, int bx,
         if (w < dw) dst[w] = acc[w];
 }
 
+// The same sums in float-float arithmetic on the FP32 pipe, for dw <= 16
+// (GB300's FP32 pipe is far wider than its FP64 one).  X and W are centred in
+// FP64 and split into two floats, v = hi + lo; a product is hi*hi exactly (the
+// rounded product and its FMA residual) plus the cross terms hi*lo + lo*hi by
+// FMA (lo*lo, about 2^-48 relative, is dropped); the chunk's products are
+// added into a float pair by error-free two-sums, and every 32-point chunk the
+// pair is flushed into an FP64 sum.  About 3 * 2^-48 relative error per
+// product and n^2 * 2^-48 per 32-term window at worst.
+template <int DW>
+__device__ __forceinline__ void gauss_cross_ff_body(const GaussArgs &A, int bx, int by,
+                                                    float2 (*sW)[kGaussMaxDims])
+{
+    const int rows = (A.S + 1) * A.dx, dw = A.dw;
+    const int row = bx * kF64Rows + threadIdx.x;
+    const bool live = row < rows;
+    const int s = live ? row / A.dx : 0, a = live ? row % A.dx : 0;
+    const int32_t *pi = s > 0 ? A.perms + (size_t)(s - 1) * A.N : nullptr;
+    const float2 *xcol = reinterpret_cast<const float2 *>(A.xc) + (size_t)a * A.N;
+    double acc[DW];
+#pragma unroll
+    for (int w = 0; w < DW; ++w) acc[w] = 0.0;
+    const int nchunks = (A.N + kGaussKC - 1) / kGaussKC;
+    const int c0 = by * A.chunks_per_split;
+    const int c1 = min(nchunks, c0 + A.chunks_per_split);
+    for (int c = c0; c < c1; ++c) {
+        const int t0 = c * kGaussKC, n = min(kGaussKC, A.N - t0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < kGaussKC * DW; e += kF64Rows) {
+            const int t = e / DW, w = e - t * DW;
+            float2 v = make_float2(0.f, 0.f);
+            if (t < n && w < dw) {
+                const double d = (double)A.base[A.cols[A.dx + w] + t0 + t] - A.mean[A.dx + w];
+                v.x = (float)d;
+                v.y = (float)(d - (double)v.x);
+            }
+            sW[t][w] = v;
+        }
+        __syncthreads();
+        if (!live) continue;
+        float sh[DW], sl[DW];
+#pragma unroll
+        for (int w = 0; w < DW; ++w) sh[w] = sl[w] = 0.f;
+        for (int t8 = 0; t8 < n; t8 += 8) {
+            // eight permutation entries, then eight X values, before any is used
+            int src[8];
+            float2 xs[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int t = min(t8 + u, n - 1);   // past n: W is zero there
+                src[u] = pi ? pi[t0 + t] : t0 + t;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) xs[u] = xcol[src[u]];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {   // t <= 31: t8 <= 24
+                const int t = t8 + u;
+                const float2 x = xs[u];
+#pragma unroll
+                for (int w = 0; w < DW; ++w) {
+                    const float2 y = sW[t][w];
+                    const float p = __fmul_rn(x.x, y.x);
+                    float e = __fmaf_rn(x.x, y.x, -p);
+                    e = __fmaf_rn(x.x, y.y, e);
+                    e = __fmaf_rn(x.y, y.x, e);
+                    const float sn = __fadd_rn(sh[w], p);
+                    const float bp = __fsub_rn(sn, sh[w]);
+                    const float er =
+                        __fadd_rn(__fsub_rn(sh[w], __fsub_rn(sn, bp)), __fsub_rn(p, bp));
+                    sl[w] = __fadd_rn(sl[w], __fadd_rn(er, e));
+                    sh[w] = sn;
+                }
+            }
+        }
+#pragma unroll
+        for (int w = 0; w < DW; ++w) acc[w] += (double)sh[w] + (double)sl[w];
+    }
+    if (!live) return;
+    double *dst = A.cross_part + ((size_t)by * rows + row) * dw;
+#pragma unroll
+    for (int w = 0; w < DW; ++w)
+        if (w < dw) dst[w] = acc[w];
+}
+
 __device__ __forceinline__ void gauss_cross_f64_any(const GaussArgs &A, int bx, int by)
 {
     __shared__ double sW[kGaussKC][kGaussMaxDims];
+    float2 (*sF)[kGaussMaxDims] = reinterpret_cast<float2 (*)[kGaussMaxDims]>(sW);
     switch ((A.dw + 1) >> 1) {
     case 0:
-    case 1: gauss_cross_f64_body<2>(A, bx, by, sW); break;
-    case 2: gauss_cross_f64_body<4>(A, bx, by, sW); break;
-    case 3: gauss_cross_f64_body<6>(A, bx, by, sW); break;
-    case 4: gauss_cross_f64_body<8>(A, bx, by, sW); break;
-    case 5: gauss_cross_f64_body<10>(A, bx, by, sW); break;
-    case 6: gauss_cross_f64_body<12>(A, bx, by, sW); break;
-    case 7: gauss_cross_f64_body<14>(A, bx, by, sW); break;
-    case 8: gauss_cross_f64_body<16>(A, bx, by, sW); break;
+    case 1: gauss_cross_ff_body<2>(A, bx, by, sF); return;
+    case 2: gauss_cross_ff_body<4>(A, bx, by, sF); return;
+    case 3: gauss_cross_ff_body<6>(A, bx, by, sF); return;
+    case 4: gauss_cross_ff_body<8>(A, bx, by, sF); return;
+    case 5: gauss_cross_ff_body<10>(A, bx, by, sF); return;
+    case 6: gauss_cross_ff_body<12>(A, bx, by, sF); return;
+    case 7: gauss_cross_ff_body<14>(A, bx, by, sF); return;
+    case 8: gauss_cross_ff_body<16>(A, bx, by, sF); return;
+    default: break;
+    }
+    switch ((A.dw + 1) >> 1) {
     case 9: gauss_cross_f64_body<18>(A, bx, by, sW); break;
     case 10: gauss_cross_f64_body<20>(A, bx, by, sW); break;
     case 11: gauss_cross_f64_body<22>(A, bx, by, sW); break;
@@ -633,7 +720,8 @@ __global__ void gauss_mean_batch(const GaussArgs *args)
     const GaussArgs A = args[blockIdx.z];
     if ((int)blockIdx.x < A.d) gauss_mean_body(A, blockIdx.x);
 }
-// xc[a][t] = x_a(t) - mean_a in FP64, grid y = X dim a
+// xc[a][t] = x_a(t) - mean_a in FP64 (as a float pair hi + lo when the
+// float-float contraction takes the estimate), grid y = X dim a
 __global__ void gauss_centre_batch(const GaussArgs *args)
 {
     const GaussArgs A = args[blockIdx.z];
@@ -641,9 +729,18 @@ __global__ void gauss_centre_batch(const GaussArgs *args)
     if (a >= A.dx) return;
     const float *col = A.base + A.cols[a];
     const double m = A.mean[a];
+    const bool ff = A.dw <= kGaussFFMaxW;   // float pairs for the float-float contraction
     double *dst = A.xc + (size_t)a * A.N;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < A.N; t += gridDim.x * blockDim.x)
-        dst[t] = (double)col[t] - m;
+    float2 *dst2 = reinterpret_cast<float2 *>(A.xc) + (size_t)a * A.N;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < A.N; t += gridDim.x * blockDim.x) {
+        const double d = (double)col[t] - m;
+        if (ff) {
+            const float hi = (float)d;
+            dst2[t] = make_float2(hi, (float)(d - (double)hi));
+        } else {
+            dst[t] = d;
+        }
+    }
 }
 __global__ void gauss_cov_batch(const GaussArgs *args)
 {
@@ -669,7 +766,7 @@ __global__ void gauss_cross_reduce_batch(const GaussArgs *args)
 __global__ void gauss_schur_f64_batch(const GaussArgs *args)
 {
     const GaussArgs A = args[blockIdx.z];
-    gauss_schur_body(A, gauss_f64_gamma(A.N), blockIdx.x * blockDim.x + threadIdx.x);
+    gauss_schur_body(A, gauss_batch_gamma(A.N, A.dw), blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 }  // namespace
