@@ -25,6 +25,11 @@ struct GaussArgs {
                             // [1] 1: a tensor-core wait timed out
     double *cross;          // [S + 1][dx][dw] cross-covariance of permuted X with W
     double *out, *err;      // [S + 1] estimates and error bounds
+    // the W-W block of the covariance and the factors can be another
+    // estimate's with the same W (own_w = 0: covw, LW, LZ, norms point there,
+    // and this estimate computes only its X rows); own_w = 1: covw = cov
+    const double *covw;
+    int own_w;
     double *xc;             // [dx][N] X columns centred in FP64, stored as float pairs
                             // (hi, lo) when dw <= kGaussFFMaxW (batched contraction only)
     // the contraction is split along the points: split p sums chunks

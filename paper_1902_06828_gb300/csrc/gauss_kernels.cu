@@ -56,6 +56,7 @@ __device__ __forceinline__ void gauss_cov_body(const GaussArgs &A, int p)
         p -= A.d - i;
         ++i;
     }
+    if (!A.own_w && i >= A.dx) return;   // a W-W entry: taken from covw
     const int j = i + p;
     const float *ci = A.base + A.cols[i];
     const float *cj = A.base + A.cols[j];
@@ -219,7 +220,7 @@ __device__ __forceinline__ void gauss_schur_body(const GaussArgs &A, double gamm
             for (int b = 0; b < dx; ++b) Sm[a * dx + b] = A.cov[a * d + b];
         double vnorm2 = 0.0, svv = 0.0;
         double vall[kGaussMaxX * kGaussMaxDims];
-        for (int r = 0; r < n; ++r) svv += A.cov[(dx + off + r) * d + dx + off + r];
+        for (int r = 0; r < n; ++r) svv += A.covw[(dx + off + r) * d + dx + off + r];
         for (int a = 0; a < dx; ++a) {
             for (int r = 0; r < n; ++r) {
                 double t = c[a * dw + off + r];
@@ -750,7 +751,7 @@ __global__ void gauss_cov_batch(const GaussArgs *args)
 __global__ void gauss_factor_batch(const GaussArgs *args)
 {
     const GaussArgs A = args[blockIdx.z];
-    gauss_factor_body(A);
+    if (A.own_w) gauss_factor_body(A);
 }
 __global__ void __launch_bounds__(kF64Rows) gauss_cross_f64_batch(const GaussArgs *args)
 {

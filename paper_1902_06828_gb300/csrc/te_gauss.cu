@@ -55,6 +55,8 @@ void gauss_bind(GaussArgs &A, double *w, bool xc = false)
     A.cross = A.scratch + kGaussMaxDims;
     A.cross_part = A.cross + (size_t)(A.S + 1) * A.dx * dw;
     A.xc = xc ? A.cross_part + (size_t)A.splits * (A.S + 1) * A.dx * dw : nullptr;
+    A.covw = A.cov;
+    A.own_w = 1;
 }
 
 // offset of variable v's column at the first point: the value at point t is
@@ -89,7 +91,7 @@ te_status run_groups_gauss(te_ctx *ctx, const std::vector<HostGroup> &groups, in
     // contraction of cmi_gauss (~1e-7) would flip near-ties.  Estimates run in
     // batches, one launch per kernel per batch; each has its own workspace.
     std::vector<GaussArgs> est;
-    std::vector<int> slot0;
+    std::vector<int> slot0, gid;   // gid: the estimate's group (same W)
     std::vector<int> cols;
     std::vector<size_t> col0;
     for (const HostGroup &g : groups) {
@@ -122,6 +124,7 @@ te_status run_groups_gauss(te_ctx *ctx, const std::vector<HostGroup> &groups, in
             A.base = g.data->d_series;
             A.perms = p1;
             est.push_back(A);
+            gid.push_back((int)(&g - groups.data()));
             slot0.push_back(ms[0]->out);
             col0.push_back(cols.size());
             for (int a = 0; a < g.dx; ++a)
@@ -164,6 +167,7 @@ te_status run_groups_gauss(te_ctx *ctx, const std::vector<HostGroup> &groups, in
     CK(cudaMemsetAsync(v_out, 0, (size_t)n_out * 8, ctx->stream), "cudaMemsetAsync");
     if (!cols.empty())
         CK(copy_h2d(ctx, cols_dev, cols.data(), cols.size() * 4), "cudaMemcpyAsync");
+    int src = 0;
     for (int i = 0; i < n_est; ++i) {
         GaussArgs &A = est[i];
         gauss_bind(A, w + off[i], true);
@@ -171,6 +175,17 @@ te_status run_groups_gauss(te_ctx *ctx, const std::vector<HostGroup> &groups, in
         A.status = status;
         A.out = v_out + slot0[i];
         A.err = v_err + slot0[i];
+        // the group's first estimate in each batch forms the W-W covariance and
+        // the factors; the group's later ones in the batch use them
+        if (i % kGaussBatch == 0 || gid[i] != gid[i - 1]) {
+            src = i;
+        } else {
+            A.own_w = 0;
+            A.covw = est[src].cov;
+            A.LW = est[src].LW;
+            A.LZ = est[src].LZ;
+            A.norms = est[src].norms;
+        }
         ctx->stats.estimates += (uint64_t)A.S + 1;
     }
     for (int b0 = 0; b0 < n_est; b0 += kGaussBatch) {
