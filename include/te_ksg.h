@@ -257,7 +257,8 @@ typedef struct {
                                       cmi_gauss (Methods, Vector autoregressive process), k
                                       unused, theiler must be 0, every estimate at most 8 X
                                       and 32 variables in all; decisions then compare the
-                                      FP64 estimates */
+                                      FP64 estimates, whose cross-covariances are summed in
+                                      float-float or FP64 arithmetic (about 1e-13 relative) */
 } te_infer_params;
 
 typedef struct {

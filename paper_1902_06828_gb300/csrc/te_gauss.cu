@@ -86,10 +86,11 @@ te_status run_groups_gauss(te_ctx *ctx, const std::vector<HostGroup> &groups, in
     // differ only in the permutation.  Member s of a candidate writes slot
     // slot0 + s and, for s >= 1, reads permutation perms + (s - 1) N.  The
     // test decisions compare these estimates, so the cross-covariances are
-    // summed in FP64 (gauss_launch_batch_f64): decisions then agree with an
-    // FP64 evaluation except at ties closer than ~1e-12, where the split-TF32
-    // contraction of cmi_gauss (~1e-7) would flip near-ties.  Estimates run in
-    // batches, one launch per kernel per batch; each has its own workspace.
+    // float-float (dw <= 16) or FP64 sums (gauss_launch_batch_f64), about
+    // 1e-13 from an FP64 evaluation: decisions then agree with it except at
+    // ties closer than that, where the split-TF32 contraction of cmi_gauss
+    // (~1e-7) would flip near-ties.  Estimates run in batches, one launch per
+    // kernel per batch; each has its own workspace.
     std::vector<GaussArgs> est;
     std::vector<int> slot0, gid;   // gid: the estimate's group (same W)
     std::vector<int> cols;

@@ -136,10 +136,11 @@ te_status finish_groups(te_ctx *ctx);
 double key_to_cmi(const te_ctx *ctx, int64_t hi, uint64_t lo, int k, int N);
 
 // The groups' estimates by the linear-Gaussian estimator (cmi_gauss's
-// pipeline with an FP64 contraction, one estimate per candidate: its members
-// must hold consecutive slots and consecutive permutations).  ctx->ws_keys receives, per slot, the
-// order-preserving int128 image of the FP64 estimate, so the test statistics
-// compare estimates; gauss_key_value inverts it.  Blocks until done.
+// pipeline with a float-float or FP64 contraction, one estimate per candidate:
+// its members must hold consecutive slots and consecutive permutations).
+// ctx->ws_keys receives, per slot, the order-preserving int128 image of the
+// FP64 estimate, so the test statistics compare estimates; gauss_key_value
+// inverts it.  Blocks until done.
 te_status run_groups_gauss(te_ctx *ctx, const std::vector<HostGroup> &groups, int n_out);
 double gauss_key_value(int64_t hi, uint64_t lo);
 
