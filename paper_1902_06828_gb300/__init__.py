@@ -307,6 +307,12 @@ def te_network_infer(ctx: Context, data: Data, *, k=4, theiler=0, max_lag_target
     adjacency [src, tgt], min lags, per-target selections and counters.
     estimator: "ksg" or "gauss" (the linear-Gaussian estimator of cmi_gauss;
     k is then unused and theiler must be 0)."""
+    modes = {"auto": 0, "trials": 1, "within": 2}
+    estimators = {"ksg": 0, "gauss": 1}
+    if surr_mode not in modes:
+        raise ValueError(f"surr_mode must be one of {sorted(modes)}, not {surr_mode!r}")
+    if estimator not in estimators:
+        raise ValueError(f"estimator must be one of {sorted(estimators)}, not {estimator!r}")
     tarr = None
     nt = 0
     if targets is not None:
@@ -316,8 +322,7 @@ def te_network_infer(ctx: Context, data: Data, *, k=4, theiler=0, max_lag_target
                          int(n_surr), float(alpha_max), float(alpha_min), float(alpha_omnibus),
                          float(alpha_seq), int(bool(seq_test)), int(bool(fdr)), float(alpha_fdr),
                          int(seed), C.cast(tarr, C.POINTER(C.c_int32)) if tarr else None, nt,
-                         int(bool(indep_surr)), {"auto": 0, "trials": 1, "within": 2}[surr_mode],
-                         {"ksg": 0, "gauss": 1}[estimator])
+                         int(bool(indep_surr)), modes[surr_mode], estimators[estimator])
     res = C.POINTER(_abi.NetworkResult)()
     st = ctx._lib.te_network_infer(ctx._h, data._h, C.byref(P), C.byref(res))
     _check(ctx._h, st)

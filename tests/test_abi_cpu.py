@@ -51,3 +51,10 @@ def test_null_arguments_rejected_without_touching_the_gpu():
     lib.te_ctx_destroy(None)
     lib.te_data_destroy(None)
     lib.te_network_result_free(None)
+
+
+def test_network_infer_rejects_unknown_modes_before_any_call():
+    import paper_1902_06828_gb300 as te
+    for kw in (dict(estimator="kraskov"), dict(surr_mode="shuffle")):
+        with pytest.raises(ValueError):
+            te.te_network_infer(None, None, **kw)
