@@ -45,7 +45,7 @@ def merge_network_shards(shards, n_proc: int, fdr: bool = False, alpha_fdr: floa
     ascending order, ties in target order; the largest rank r with
     p_(r) <= alpha_fdr r / m and every smaller one rejected), and a target not
     rejected loses its sources.  Then the adjacency [src, tgt] and the
-    smallest selected lag per link."""
+    smallest selected lag per link; seconds is the slowest shard's time."""
     import numpy as np
     targets = sorted((dict(t) for sh in shards for t in sh["targets"]), key=lambda t: t["target"])
     seen = [t["target"] for t in targets]
@@ -72,7 +72,9 @@ def merge_network_shards(shards, n_proc: int, fdr: bool = False, alpha_fdr: floa
             if lag[src, t["target"]] == 0 or l < lag[src, t["target"]]:
                 lag[src, t["target"]] = l
     return dict(adjacency=adj, min_lag=lag, targets=targets,
-                n_estimates=sum(int(sh["n_estimates"]) for sh in shards))
+                n_estimates=sum(int(sh["n_estimates"]) for sh in shards),
+                seconds=max([float(sh.get("seconds", 0.0)) for sh in shards] or [0.0]),
+                theiler=next((sh["theiler"] for sh in shards if "theiler" in sh), None))
 
 
 def infer_network_sharded(ctx, data, n_proc: int, dist=None, fdr: bool = False,
@@ -88,5 +90,5 @@ def infer_network_sharded(ctx, data, n_proc: int, dist=None, fdr: bool = False,
     mine = shard_targets(n_proc, rank, world)
     res = te.te_network_infer(ctx, data, targets=mine, fdr=False, **params) if mine else \
         dict(targets=[], n_estimates=0)
-    shard = dict(targets=res["targets"], n_estimates=res["n_estimates"])
+    shard = {k: res[k] for k in ("targets", "n_estimates", "seconds", "theiler") if k in res}
     return merge_network_shards(gather_results(dist, shard), n_proc, fdr, alpha_fdr)

@@ -30,5 +30,6 @@ def test_one_rank_sharded_inference_equals_library_fdr():
                 assert u["sel_sources"] == v["sel_sources"]
                 assert u["significant"] == v["significant"]
             assert sh["n_estimates"] == lib["n_estimates"]
+            assert sh["theiler"] == lib["theiler"]
     finally:
         ctx.close()
