@@ -310,6 +310,31 @@ te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_para
                            te_network_result **out);
 void te_network_result_free(te_network_result *res);
 
+/*
+ * Request trace of te_network_infer (for verification against an independent
+ * implementation of the same greedy loop; Methods, "Inference algorithm" steps
+ * 1-4).  With a callback set, every test a target runs is reported once, after
+ * its estimates are computed and before its decision is taken:
+ *   target, stage (1 target past, 2 sources past, 3 pruning, 4 omnibus,
+ *   5 step-down), iteration of the stage (0 for stages 4 and 5),
+ *   vars[n_vars]: the candidates in the order of the request (stages 1, 2, 3,
+ *   5: one variable per candidate, n_cand == n_vars; stage 4: the selected
+ *   sources block, one candidate),
+ *   keys[2 * n_cand * (n_surr + 1)]: candidate-major, slot c * (n_surr + 1) + s
+ *   (s = 0 the original, s >= 1 surrogate s) as (hi, lo) 128-bit two's
+ *   complement pairs: the exact KSG digamma key, or with estimator 1 the
+ *   order-preserving integer image of the FP64 estimate.
+ * The pointers are valid during the callback only.  Tracing copies every key
+ * of a round to the host once per round.  fn = NULL switches tracing off.
+ * The callback runs on the calling thread, inside te_network_infer; it must
+ * not call into the library with the same context.  Errors: TE_EINVAL for a
+ * NULL context.
+ */
+typedef void (*te_trace_fn)(void *user, int32_t target, int32_t stage, int32_t iter,
+                            const te_var *vars, int32_t n_vars, int32_t n_cand,
+                            int32_t n_surr, const int64_t *keys);
+te_status te_ctx_set_trace(te_ctx *ctx, te_trace_fn fn, void *user);
+
 /* Counters of a context since its creation. */
 typedef struct {
     uint64_t estimates;       /* CMI estimates (members) evaluated */
@@ -399,24 +424,31 @@ te_status te_serve_get_stats(te_ctx *ctx, te_serve_stats *out);
  * Its scratch memory (surrogate permutations, digamma table, launch
  * descriptors, accumulators, keys) is one file-scope device array of
  * TE_STATIC_SCRATCH_BYTES that every GPU which loads this library holds until
- * the process exits.  A call needs
- *   8 (N + 2) + 4 S N + 48 (S + 1) + 4 (dx + dy + dz)  bytes (each part
- *   rounded up to 256), N = T - max_lag, S = n_surr <= TE_STATIC_MAX_SURR,
- * and returns TE_EINVAL when that exceeds TE_STATIC_SCRATCH_BYTES.
+ * the process exits.  A call needs the sum of seven parts, each rounded up to
+ * a multiple of 256 bytes:
+ *   8 (N + 2)            digamma table
+ *   4 S N                surrogate permutations
+ *   256                  group descriptor (one, at most 256 bytes)
+ *   24 (S + 1)           member descriptors
+ *   4 (dx + dy + dz)     column offsets
+ *   16 (S + 1), twice    key accumulators and keys
+ * with N = T - max_lag and S = n_surr <= TE_STATIC_MAX_SURR; it returns
+ * TE_EINVAL when the sum exceeds TE_STATIC_SCRATCH_BYTES.
  *
  * series_dev: device float32 [n_proc][T] on the current device, owned by the
- * caller.  x, y, z, params: as cmi_ksg.  cuda_stream: a cudaStream_t of the
+ * caller; TE_EINVAL if it is not device memory of the current device.  x, y, z, params: as cmi_ksg.  cuda_stream: a cudaStream_t of the
  * current device or NULL (legacy default stream); the call synchronises it.
  * out_cmi: host double[1 + S]; out_key: NULL or host int64[2 (1 + S)].
  * Errors: status codes only (no context carries a message): TE_EINVAL for any
  * rule cmi_ksg checks plus the scratch limit, TE_ECUDA for a failed CUDA call.
  *
  * The first call on a device resolves the device address of the scratch array
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls share the array, which keeps the last
- * call's contents; each call clears what must start at zero.  Calls whose work
- * overlaps on the GPU race on the array, and calls from several host threads
- * race on static host buffers: serialise them. */
+ * (cudaGetSymbolAddress, with that device current).  No call may be made while
+ * its stream is being captured into a CUDA graph: each call copies from host
+ * staging buffers and synchronises the stream.  All calls share the array,
+ * which keeps the last call's contents; each call clears what must start at
+ * zero.  Calls whose work overlaps on the GPU race on the array, and calls
+ * from several host threads race on static host buffers: serialise them. */
 #define TE_STATIC_SCRATCH_BYTES (32u << 20)
 #define TE_STATIC_MAX_SURR 4095
 te_status cmi_ksg_static(const float *series_dev, int32_t n_proc, int32_t T, const te_var *x,

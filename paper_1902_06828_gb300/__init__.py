@@ -79,6 +79,27 @@ class Context:
             stream = stream.cuda_stream
         _check(self._h, self._lib.te_ctx_set_stream(self._h, C.c_void_p(stream or 0)))
 
+    def set_trace(self, fn=None):
+        """fn(target, stage, iter, vars, n_cand, n_surr, keys) is called by
+        te_network_infer once per test, before its decision: vars a list of
+        (proc, lag), keys a list of n_cand lists of n_surr + 1 Python ints
+        (128-bit keys, candidate-major).  None switches tracing off."""
+        if fn is None:
+            self._trace_cb = None
+            _check(self._h, self._lib.te_ctx_set_trace(self._h, _abi.TRACE_FN(), None))
+            return
+
+        def cb(_user, target, stage, it, vars_p, n_vars, n_cand, n_surr, keys_p):
+            vs = [(vars_p[i].proc, vars_p[i].lag) for i in range(n_vars)]
+            m = n_cand * (n_surr + 1)
+            raw = np.ctypeslib.as_array(keys_p, shape=(2 * m,)).copy()
+            flat = _keys_to_int(raw)
+            keys = [flat[c * (n_surr + 1):(c + 1) * (n_surr + 1)] for c in range(n_cand)]
+            fn(int(target), int(stage), int(it), vs, int(n_cand), int(n_surr), keys)
+
+        self._trace_cb = _abi.TRACE_FN(cb)   # kept alive while the library holds it
+        _check(self._h, self._lib.te_ctx_set_trace(self._h, self._trace_cb, None))
+
     def stats(self) -> dict:
         s = _abi.Stats()
         _check(self._h, self._lib.te_get_stats(self._h, C.byref(s)))
@@ -441,7 +462,12 @@ def cmi_ksg_static(series_dev, x, y, z=(), *, k=4, theiler=0, max_lag=None, n_su
     t = series_dev
     if not (hasattr(t, "is_cuda") and t.is_cuda) or str(t.dtype) != "torch.float32":
         raise TEError(_abi.TE_EINVAL, "series_dev must be a CUDA float32 tensor")
-    t = t.contiguous()
+    import torch
+    if t.device.index != torch.cuda.current_device():
+        raise TEError(_abi.TE_EINVAL, "series_dev must live on the current CUDA device")
+    if t.dim() != 2 or not t.is_contiguous():
+        # a copy would allocate device memory, which this entry point promises not to do
+        raise TEError(_abi.TE_EINVAL, "series_dev must be a contiguous [n_proc][T] tensor")
     n_proc, T = t.shape
     if max_lag is None:
         max_lag = _default_max_lag(x, y, z)

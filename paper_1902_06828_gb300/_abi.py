@@ -80,6 +80,9 @@ class ServeStats(C.Structure):
 # every symbol include/te_ksg.h declares: name -> (restype, argtypes)
 _P = C.c_void_p
 _I32 = C.c_int32
+# te_trace_fn(user, target, stage, iter, vars, n_vars, n_cand, n_surr, keys)
+TRACE_FN = C.CFUNCTYPE(None, _P, _I32, _I32, _I32, C.POINTER(TeVar), _I32, _I32, _I32,
+                       C.POINTER(C.c_int64))
 SIGNATURES = {
     "te_ctx_create": (C.c_int, [C.c_int, C.POINTER(_P)]),
     "te_ctx_set_stream": (C.c_int, [_P, _P]),
@@ -98,6 +101,7 @@ SIGNATURES = {
     "te_network_infer": (C.c_int, [_P, _P, C.POINTER(InferParams),
                                    C.POINTER(C.POINTER(NetworkResult))]),
     "te_network_result_free": (None, [C.POINTER(NetworkResult)]),
+    "te_ctx_set_trace": (C.c_int, [_P, TRACE_FN, _P]),
     "te_autocorr_decay": (C.c_int, [_P, _P, _I32, C.POINTER(C.c_int32)]),
     "te_alu_peak": (C.c_int, [_P, _I32, C.POINTER(C.c_double)]),
     "te_data_create_trials": (C.c_int, [_P, _P, _I32, _I32, _I32, _I32, C.c_int, _P]),

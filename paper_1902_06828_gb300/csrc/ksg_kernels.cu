@@ -1654,6 +1654,22 @@ const void *select_kernel(const KsgVariant &v, bool dx1)
 
 }  // namespace
 
+// cudaFuncSetAttribute acts on the current device, so a launcher that raises a
+// kernel's dynamic shared-memory limit remembers that per device, not per
+// process: the first launch on a second GPU sets it again.
+constexpr int kAttrDevices = 64;
+static cudaError_t smem_attr_once(const void *f, int bytes, bool (&done)[kAttrDevices])
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < kAttrDevices && done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < kAttrDevices) done[dev] = true;
+    return cudaSuccess;
+}
+
 cudaError_t ksg_prepare_attributes()
 {
     const KsgVariant vs[] = {{4, 4, QT},  {2, 0, QT},
@@ -1679,13 +1695,12 @@ cudaError_t ksg_prepare_attributes()
 cudaError_t launch_value_sort(const ValueSortJob *jobs, int n_jobs, cudaStream_t st)
 {
     if (n_jobs <= 0) return cudaSuccess;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(&value_sort_kernel),
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kMaxOrderN * 4);
+    static bool attr_done[kAttrDevices] = {};
+    {
+        const cudaError_t e =
+            smem_attr_once(reinterpret_cast<const void *>(&value_sort_kernel),
+                           kMaxOrderN * 4, attr_done);
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     value_sort_kernel<<<n_jobs, 1024, kMaxOrderN * 4, st>>>(jobs);
     return cudaGetLastError();
@@ -1799,13 +1814,12 @@ cudaError_t launch_perms(int32_t *out, long long stride, int n, uint64_t seed, u
     if (n_perm <= 0) return cudaSuccess;
     const size_t smem = (size_t)n * sizeof(int32_t);
     const int in_smem = smem <= 200 * 1024;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(&fisher_yates_kernel),
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
+    static bool attr_done[kAttrDevices] = {};
+    {
+        const cudaError_t e =
+            smem_attr_once(reinterpret_cast<const void *>(&fisher_yates_kernel),
+                           200 * 1024, attr_done);
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     // permutation and draws in shared memory when both fit, else the
     // permutation alone, else neither
@@ -1890,13 +1904,12 @@ cudaError_t launch_perms_trials(int32_t *out, int R, int n, uint64_t seed, uint6
     if (n_perm <= 0) return cudaSuccess;
     if (R < 1 || n < 1 || (mode != 0 && mode != 1) || (long long)R * n >= (1LL << 31))
         return cudaErrorInvalidValue;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(
-            reinterpret_cast<const void *>(&fisher_yates_trials_kernel),
-            cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    static bool attr_done[kAttrDevices] = {};
+    {
+        const cudaError_t e =
+            smem_attr_once(reinterpret_cast<const void *>(&fisher_yates_trials_kernel),
+                           200 * 1024, attr_done);
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     const size_t whole = (size_t)R * n * sizeof(int32_t);
     size_t smem;
@@ -1918,13 +1931,12 @@ cudaError_t launch_perms_multi(const PermJob *jobs, int n_jobs, long long total,
 {
     if (n_jobs <= 0 || total <= 0) return cudaSuccess;
     if (total > 0x7fffffffLL) return cudaErrorInvalidValue;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(
-            reinterpret_cast<const void *>(&fisher_yates_multi_kernel),
-            cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    static bool attr_done[kAttrDevices] = {};
+    {
+        const cudaError_t e =
+            smem_attr_once(reinterpret_cast<const void *>(&fisher_yates_multi_kernel),
+                           200 * 1024, attr_done);
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     if (max_n <= 65535) {
         // every job shuffles in 16 bits (2 bytes per point), one warp per CTA

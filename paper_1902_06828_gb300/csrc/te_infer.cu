@@ -353,6 +353,22 @@ te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_para
             const int *ib = (const int *)(pin + ioff);
             const long long *ob = (const long long *)(pin + ooff);
 
+            // ---- optional trace: every request's keys, before its decision ----
+            if (ctx->trace_fn) {
+                std::vector<int64_t> kh((size_t)n_out * 2);
+                CK(cudaMemcpyAsync(kh.data(), ctx->ws_keys.p, kh.size() * 8,
+                                   cudaMemcpyDeviceToHost, ctx->stream),
+                   "cudaMemcpyAsync");
+                CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+                for (int a : active) {
+                    const TargetState &t = ts[a];
+                    const int iter = (t.stage == ST_OMNIBUS || t.stage == ST_SEQ) ? 0 : t.it;
+                    ctx->trace_fn(ctx->trace_user, t.target, t.stage, iter, t.order.data(),
+                                  (int32_t)t.order.size(), t.n_cand, S,
+                                  kh.data() + 2 * (size_t)t.out_base);
+                }
+            }
+
             // ---- decisions ----
             for (int a : active) {
                 TargetState &t = ts[a];
@@ -480,6 +496,14 @@ te_status te_network_infer(te_ctx *ctx, const te_data *data, const te_infer_para
     } catch (...) {
         return fail(ctx, TE_EINTERNAL, "unexpected C++ exception");
     }
+}
+
+te_status te_ctx_set_trace(te_ctx *ctx, te_trace_fn fn, void *user)
+{
+    if (!ctx) return TE_EINVAL;
+    ctx->trace_fn = fn;
+    ctx->trace_user = fn ? user : nullptr;
+    return TE_OK;
 }
 
 void te_network_result_free(te_network_result *res)

@@ -84,6 +84,8 @@ struct te_ctx {
     cudaStream_t aux_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int prepared = 0;
+    te_trace_fn trace_fn = nullptr;   // te_ctx_set_trace
+    void *trace_user = nullptr;
 };
 
 namespace teksg {

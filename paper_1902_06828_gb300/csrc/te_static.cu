@@ -14,8 +14,10 @@
 //
 // Host code never uses the array's name as an address: the first call on a
 // device (with that device current) resolves the array's device address with
-// cudaGetSymbolAddress and keeps it for later calls on that device.  Make that
-// first call before any stream capture begins.
+// cudaGetSymbolAddress and keeps it for later calls on that device.  No call
+// may be made while its stream is being captured into a CUDA graph: every
+// call copies from host staging buffers and ends by synchronising the stream,
+// and neither is allowed during capture.
 //
 // Every call shares the array and leaves its contents behind; the parts that
 // must start at zero (the key accumulators) are cleared by each call.  Two
@@ -52,6 +54,7 @@ unsigned char g_desc_host[sizeof(GroupDesc) + (kStaticMaxSurr + 1) * sizeof(Memb
 int64_t g_keys_host[2 * (kStaticMaxSurr + 1)];
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+static_assert(sizeof(GroupDesc) <= 256, "the documented scratch size counts 256 bytes for it");
 
 te_status setup_device(int dev)
 {
@@ -106,6 +109,16 @@ extern "C" te_status cmi_ksg_static(const float *series_dev, int32_t n_proc, int
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return TE_ECUDA;
+    // the series must be device memory of the current device: a pointer into
+    // another GPU's memory would be read remotely or fault
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, series_dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return TE_EINVAL;
+    }
+    if ((pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) ||
+        pa.device != dev)
+        return TE_EINVAL;
     te_status st = setup_device(dev);
     if (st) return st;
     cudaStream_t stream = (cudaStream_t)cuda_stream;

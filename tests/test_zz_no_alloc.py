@@ -69,3 +69,23 @@ def test_static_rejects_sizes_beyond_its_scratch(env):
         te.cmi_ksg_static(dev, [(0, 1)], [(1, 0)], [], k=4, max_lag=1, n_surr=5000)
     with pytest.raises(te.TEError, match="TE_EINVAL"):   # 4 S N bytes > 32 MiB
         te.cmi_ksg_static(dev, [(0, 1)], [(1, 0)], [], k=4, max_lag=1, n_surr=1000)
+
+
+def test_static_rejects_series_not_on_the_current_device(env):
+    torch, te, ctx = env
+    import ctypes as C
+    from paper_1902_06828_gb300 import _abi
+    lib = _abi.load()
+    host = np.zeros((3, 1000), np.float32)
+    xv = (_abi.TeVar * 1)(_abi.TeVar(0, 1))
+    yv = (_abi.TeVar * 1)(_abi.TeVar(1, 0))
+    p = _abi.KsgParams(4, 0, 1, 3, 0, 0)
+    out = np.zeros(4, np.float64)
+    # a host pointer is refused by the C entry point before any launch
+    st = lib.cmi_ksg_static(C.c_void_p(host.ctypes.data), 3, 1000, xv, 1, yv, 1, None, 0,
+                            C.byref(p), None, out.ctypes.data, None)
+    assert st == _abi.TE_EINVAL
+    # a non-contiguous tensor is refused by the binding instead of being copied
+    dev = torch.zeros((1000, 3), dtype=torch.float32, device="cuda").t()
+    with pytest.raises(te.TEError, match="TE_EINVAL"):
+        te.cmi_ksg_static(dev, [(0, 1)], [(1, 0)], [], k=4, max_lag=1, n_surr=3)
