@@ -1,16 +1,18 @@
 """Benchmark: KSG CMI estimates per second (surrogates included) at T = 10000.
 
-Workload (default "var10"): full greedy multivariate TE network inference on a
-seeded 10-node linear VAR (directed ER graph p = 0.3, self coupling 0.5,
-couplings U(0.1, 0.5) at random lags 1-5, spectral radius 0.9, sigma = 1),
-T = 10000 float32 samples, max lag 5, KSG k = 4, 200 surrogates per test,
-alpha = 0.05.  One step = te_network_infer over every target (all rows of
-the hot path: embeddings, permutations, fused kNN + counts + digamma keys,
-test statistics, greedy control, network assembly).
+Workload (default "clm100"): 100-node coupled logistic maps (directed ER
+graph, expected in-degree 3, lags 1-5, x_i(t) = f(0.5 x_i(t-1) + 0.5 mean_j
+x_j(t - d_ji)) + N(0, 0.1^2) mod 1, f(x) = 4x(1-x)), T = 10000 float32
+samples, max lag 5, KSG k = 4, 200 surrogates per test, alpha = 0.05.  One
+step = the complete greedy inference of one target (te_network_infer with
+that target: embeddings, permutations, fused kNN + counts + digamma keys,
+test statistics, greedy control), the steps cycling through the targets
+(warm-up steps take targets 0 .. W-1, timed steps the next K).  "var10"
+instead infers the whole 10-node VAR network per step.
 
 value : estimates / s with the series already resident on the device.
 e2e   : the same through the C ABI from a host buffer: each step uploads the
-        series (te_data_create from host memory) and reads results back.
+        series (te_data_create from pinned host memory) and reads results back.
 Under torchrun each rank infers its own replica data set (seed + rank), no
 collective on the data path ("scaling": "weak").
 
@@ -35,7 +37,6 @@ sys.path.insert(0, ROOT)
 METRIC = "KSG CMI estimates/s incl. surrogates at T=10000"
 UNIT = "estimates/s"
 TRAFFIC_PER_MEMBER_POINT = (146434560.0 + 4099584.0) / (9045 * 3995)
-SM_COUNT = 152
 
 
 def _peaks():
@@ -121,10 +122,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_sample(series, params, budget_s=20.0, members=None):
+def cpu_oracle_sample(series, params, budget_s=20.0, members=None, threads=None):
     """Time the oracle on members of the first step-2 group of target 0
     (Y = target present, Z = its lag-1 past, X = each source candidate,
-    identity plus surrogates), all host cores."""
+    identity plus surrogates), all host cores (or `threads` of them)."""
     from oracle import ksg as oksg
     n_proc, T = series.shape
     t0 = max(params["max_lag_target"], params["max_lag_sources"])
@@ -132,7 +133,7 @@ def cpu_oracle_sample(series, params, budget_s=20.0, members=None):
     cands = [(q, l) for q in range(1, n_proc) for l in range(1, params["max_lag_sources"] + 1)]
     S = 7
     perms = np.stack([oksg.permutation(params["seed"], 0, 2, 0, s, N) for s in range(1, S + 1)])
-    threads = oksg.max_threads()
+    threads = threads or oksg.max_threads()
     # calibrate with one member per thread, then size the sample to the budget
     def run(nm):
         xs, pidx = [], []
@@ -152,7 +153,8 @@ def cpu_oracle_sample(series, params, budget_s=20.0, members=None):
     return {"value": members / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": (f"{members} members (step-2 group of target 0: source candidates x "
                        f"identity/7 surrogates, Z = target lag 1) at N={N}, brute-force C "
-                       f"oracle, {threads} OpenMP threads, {dt:.1f} s")}
+                       f"oracle, {threads} OpenMP thread{'s' if threads > 1 else ''}, "
+                       f"{dt:.1f} s")}
 
 
 def plain_path(te, ctx, data, params, calls, stream):
@@ -375,6 +377,25 @@ def run_gauss_network(args):
     print(json.dumps(line), flush=True)
 
 
+def var10_network(te, ctx, stream, T):
+    """The whole 10-node VAR network (all targets) once, as an extra figure
+    beside the per-target headline: estimates per second of device time."""
+    import torch
+    series, params, desc = _workload("var10", T, 1)
+    data = te.te_data_create(ctx, series)
+    te.te_network_infer(ctx, data, **params)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    r = te.te_network_infer(ctx, data, **params)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    data.close()
+    return {"value": r["n_estimates"] / (ms / 1e3), "unit": UNIT, "ms": ms,
+            "estimates": r["n_estimates"], "workload": desc, "edges": int(r["adjacency"].sum())}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -382,10 +403,12 @@ def run_reference(args):
     series, params, desc = _workload(args.workload, args.T, 1)
     from oracle import ksg as oksg
     threads = oksg.max_threads()
-    # size one step to ~20 s of CPU work
+    # size one step so that all steps take about two minutes of CPU work (at
+    # most 20 s each)
     calib = cpu_oracle_sample(series, params, members=threads)
     per_member = 1.0 / calib["value"]          # seconds per member with all threads busy
-    members = max(threads, int(20.0 / per_member) // threads * threads)
+    budget = min(20.0, 120.0 / max(args.steps, 1))
+    members = max(threads, int(budget / per_member) // threads * threads)
     for _ in range(args.warmup):
         cpu_oracle_sample(series, params, members=threads)
     vals = []
@@ -412,14 +435,16 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="var10")
+    ap.add_argument("--workload", default="clm100")
     ap.add_argument("--T", type=int, default=10000)
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--no-extra", dest="extra", action="store_false",
+                    help="skip the extra var10 whole-network figure")
     ap.add_argument("--targets", default="all", help="comma list of targets, or 'all'")
     ap.add_argument("--serve", action="store_true",
                     help="run the serving workload instead of the network benchmark")
@@ -455,6 +480,10 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     series, params, desc = _workload(args.workload, args.T, 1 + rank)
+    n_proc = series.shape[0]
+    # clm100 (the default): one target per step, cycling through the targets;
+    # var10: the whole network per step; --targets: that list every step
+    per_target = args.targets == "all" and args.workload == "clm100"
     if args.targets != "all":
         params["targets"] = [int(v) for v in args.targets.split(",")]
         desc += f", targets {args.targets}"
@@ -464,13 +493,19 @@ def main():
     ctx.set_stream(stream)
     data = te.te_data_create(ctx, series)
     flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    counter = [0]
 
     def step(d):
+        if per_target:
+            t = counter[0] % n_proc
+            counter[0] += 1
+            return te.te_network_infer(ctx, d, targets=[t], **params)
         return te.te_network_infer(ctx, d, **params)
 
     for _ in range(args.warmup):
         step(data)
     torch.cuda.synchronize()
+    first_timed = counter[0]
 
     def barrier():
         if dist:
@@ -494,9 +529,13 @@ def main():
     clk = clocks.stop()
     s1 = ctx.stats()
     ms = ev0.elapsed_time(ev1)
+    if per_target:
+        last = counter[0] - 1
+        desc += (f"; one step = the complete greedy inference of one target; warm-up targets "
+                 f"0-{first_timed - 1}, timed targets {first_timed}-{last} (mod {n_proc})")
 
     # end to end through the C ABI with host buffers
-    e2e_steps = args.e2e_steps if args.e2e_steps is not None else args.steps
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else min(args.steps, 3)
     host = torch.from_numpy(series).pin_memory()
     e_est = 0
     sb = ctx.stats()
@@ -530,7 +569,8 @@ def main():
     ksg_launches = s1["ksg_launches"] - s0["ksg_launches"]
     ops = s1["ksg_ops"] - s0["ksg_ops"]
     achieved = ops / (kernel_ms / 1e3) / 1e12 if kernel_ms > 0 else None
-    peak = SM_COUNT * 128 * sm_max * 1e6 / 1e12
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = sm_count * 128 * sm_max * 1e6 / 1e12
     # DRAM traffic of the KSG kernel per launch: the ncu capture of the same
     # kernel (T = 4000, step-2 launch of target 0, 9045 members x 3995 points)
     # read 146.43 MB and wrote 4.10 MB, i.e. 4.17 bytes per member-point (each
@@ -570,7 +610,8 @@ def main():
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "kernel": "ksg_lane_kernel", "kernel_ms_per_launch":
                      kernel_ms / max(ksg_launches, 1), "launches": ksg_launches,
-                     "peak_note": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived)",
+                     "peak_note": f"{sm_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
+                                  "(derived; SM count read from the device)",
                      "peak_measured_mix": peak_mix,
                      "frac_of_measured_mix": (achieved / peak_mix) if achieved and peak_mix
                      else None,
@@ -589,8 +630,12 @@ def main():
     if args.plain_calls > 0:
         line["plain_path"] = plain_path(te, ctx, data, params, args.plain_calls, stream)
         line["plain_path"]["batched_over_plain"] = value / line["plain_path"]["value"]
+    if args.extra and args.workload != "var10" and world == 1:
+        line["var10_network"] = var10_network(te, ctx, stream, args.T)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_oracle_sample(series, params)
+        one = cpu_oracle_sample(series, params, members=3, threads=1)
+        line["cpu_baseline"]["one_core"] = {"value": one["value"], "sample": one["sample"]}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
