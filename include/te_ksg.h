@@ -335,6 +335,35 @@ typedef void (*te_trace_fn)(void *user, int32_t target, int32_t stage, int32_t i
                             int32_t n_surr, const int64_t *keys);
 te_status te_ctx_set_trace(te_ctx *ctx, te_trace_fn fn, void *user);
 
+/* ---- execution options (tuning and measurement; the paper has no counterpart) --
+ *
+ * te_ctx_set_option sets one option of a context for its later calls:
+ *   TE_OPT_KSG_TILE              points per staged tile of the member-lane KSG
+ *                                kernel: 64, 128 or 256; 0 (default) = the
+ *                                compiled tuning table, chosen by points,
+ *                                conditioning dimensions and group size
+ *   TE_OPT_KSG_MEMBERS_PER_LANE  1 or 2 (2 only where every group of a launch
+ *                                has at least 64 members); 0 (default) = the
+ *                                tuning table
+ *   TE_OPT_PERSISTENT            1: member-lane launches run as persistent
+ *                                grids (as many CTAs as are resident at once,
+ *                                each taking query-tile x member-block items
+ *                                from a device counter); 0 (default): one CTA
+ *                                per item
+ *   TE_OPT_GRAPH                 1: each batch's device work (point orders,
+ *                                X-value rows, KSG kernels, finalize) is
+ *                                captured into a CUDA graph on the context's
+ *                                stream and launched as one graph; 0 (default):
+ *                                direct launches.  The stream must not be
+ *                                capturing already.
+ * None of them changes a result.  Errors: TE_EINVAL for an unknown option or
+ * value. */
+#define TE_OPT_KSG_TILE 1
+#define TE_OPT_KSG_MEMBERS_PER_LANE 2
+#define TE_OPT_PERSISTENT 3
+#define TE_OPT_GRAPH 4
+te_status te_ctx_set_option(te_ctx *ctx, int32_t option, int64_t value);
+
 /* Counters of a context since its creation. */
 typedef struct {
     uint64_t estimates;       /* CMI estimates (members) evaluated */

@@ -79,6 +79,14 @@ class Context:
             stream = stream.cuda_stream
         _check(self._h, self._lib.te_ctx_set_stream(self._h, C.c_void_p(stream or 0)))
 
+    def set_option(self, name: str, value: int):
+        """Execution options (no change to any result): "ksg_tile" (64, 128,
+        256; 0 = tuning table), "ksg_members_per_lane" (1, 2; 0 = tuning
+        table), "persistent" (0/1), "graph" (0/1)."""
+        if name not in _abi.OPTIONS:
+            raise ValueError(f"unknown option {name!r}; one of {sorted(_abi.OPTIONS)}")
+        _check(self._h, self._lib.te_ctx_set_option(self._h, _abi.OPTIONS[name], int(value)))
+
     def set_trace(self, fn=None):
         """fn(target, stage, iter, vars, n_cand, n_surr, keys) is called by
         te_network_infer once per test, before its decision: vars a list of

@@ -77,6 +77,9 @@ class ServeStats(C.Structure):
                 ("pending", C.c_uint64)]
 
 
+# te_ctx_set_option options (include/te_ksg.h)
+OPTIONS = {"ksg_tile": 1, "ksg_members_per_lane": 2, "persistent": 3, "graph": 4}
+
 # every symbol include/te_ksg.h declares: name -> (restype, argtypes)
 _P = C.c_void_p
 _I32 = C.c_int32
@@ -102,6 +105,7 @@ SIGNATURES = {
                                    C.POINTER(C.POINTER(NetworkResult))]),
     "te_network_result_free": (None, [C.POINTER(NetworkResult)]),
     "te_ctx_set_trace": (C.c_int, [_P, TRACE_FN, _P]),
+    "te_ctx_set_option": (C.c_int, [_P, _I32, C.c_int64]),
     "te_autocorr_decay": (C.c_int, [_P, _P, _I32, C.POINTER(C.c_int32)]),
     "te_alu_peak": (C.c_int, [_P, _I32, C.POINTER(C.c_double)]),
     "te_data_create_trials": (C.c_int, [_P, _P, _I32, _I32, _I32, _I32, C.c_int, _P]),

@@ -21,7 +21,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libte_ksg.so")
 SOURCES = ["ksg_kernels.cu", "te_runtime.cu", "te_infer.cu", "te_static.cu", "te_serve.cu",
            "gauss_kernels.cu", "te_gauss.cu", "te_theiler.cu", "te_peak.cu"]
-HEADERS = ["ksg_internal.h", "te_runtime.h", "gauss_internal.h"]
+HEADERS = ["ksg_internal.h", "te_runtime.h", "gauss_internal.h", "ksg_tune_table.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -99,6 +99,10 @@ struct KsgLaunch {
     // xval[r * xpitch + j] (positions in the group's order, zero past N)
     const float *xval;
     long long xpitch;
+    // persistent member-lane grid (nullptr: one CTA per item): items are taken
+    // from this counter, zeroed before the launch; n_items = items of the launch
+    unsigned long long *item_counter;
+    long long n_items;
 };
 
 // Kernel variants: members per thread and k.  kgen = 0 means k is a template
@@ -110,6 +114,7 @@ struct KsgVariant {
     int qt;     // threads per CTA
     bool tma;   // member-lane kernel: X tiles copied by the tensor memory accelerator
                 // from the launch's X-value rows (false: gathered by the threads)
+    bool persist = false;   // member-lane TMA kernel as a persistent grid (KsgLaunch::item_counter)
 };
 
 // member-lane kernel (single-variable X): 32 members x 32 query points per CTA
@@ -131,7 +136,10 @@ inline size_t ksg_lane_tma_smem_bytes(int dyz, int jt, int members)
            (size_t)warps * (2 * 4 * 8 * 4 + 4 * 4 * (size_t)dyz + 4 * (size_t)(jt / 64));
 }
 
-// tmap: the 2-D tensor map of L.xval for TMA variants (nullptr otherwise)
+// tmap: the 2-D tensor map of L.xval for TMA variants (nullptr otherwise).
+// With v.persist (member-lane TMA kernels only; L.item_counter set) the grid is persistent:
+// as many CTAs as fit on the device at once, each taking items from the
+// counter.
 cudaError_t launch_ksg(const KsgLaunch &L, const KsgVariant &v, long long n_items, bool dx1,
                        size_t smem_bytes, cudaStream_t st, const CUtensorMap *tmap = nullptr);
 // X-value rows of every member of the launch (L.xval, row pitch L.xpitch floats)

@@ -602,15 +602,17 @@ __device__ __forceinline__ bool tile_wait(uint32_t addr, uint32_t parity)
     return false;
 }
 
+// One work item of the member-lane kernel: query tile x member block `item`
+// of the launch (the CTA's whole job in an ordinary grid; one of many in a
+// persistent one).
 template <int KT, int MS, bool TMA>
-__global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
-    ksg_lane_kernel(const KsgLaunch L, const __grid_constant__ CUtensorMap tmx)
+__device__ __forceinline__ void ksg_lane_item(const KsgLaunch &L, const CUtensorMap &tmx,
+                                              const long long item)
 {
     constexpr int KB = KT > 0 ? KT : KMAX;
     constexpr int MB = 32 * MS;   // members per CTA: MS per lane
     extern __shared__ __align__(16) float smem[];
 
-    const long long item = blockIdx.x;
     int glo = 0, ghi = L.n_groups - 1;
     while (glo < ghi) {
         const int mid = (glo + ghi + 1) >> 1;
@@ -1184,6 +1186,36 @@ __global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
     }
 }
 
+template <int KT, int MS, bool TMA>
+__global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
+    ksg_lane_kernel(const KsgLaunch L, const __grid_constant__ CUtensorMap tmx)
+{
+    ksg_lane_item<KT, MS, TMA>(L, tmx, blockIdx.x);
+}
+
+template <int KT, int MS, bool TMA>
+__global__ void __launch_bounds__(LW * 32, (KT > 0 && MS == 1) ? 3 : 2)
+    ksg_lane_persistent_kernel(const KsgLaunch L, const __grid_constant__ CUtensorMap tmx)
+{
+    // Persistent grid: every CTA takes its next item from a device counter
+    // (zeroed before the launch) until none is left, or until a tile copy has
+    // timed out somewhere (the error flag is read by one thread and the
+    // decision shared, so the CTA leaves together).
+    __shared__ long long s_item;
+    long long item = blockIdx.x;
+    while (item < L.n_items) {
+        ksg_lane_item<KT, MS, TMA>(L, tmx, item);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned long long bad = *(volatile const unsigned long long *)(L.work + 2);
+            s_item = bad ? L.n_items
+                         : (long long)atomicAdd(L.item_counter, 1ull) + (long long)gridDim.x;
+        }
+        __syncthreads();
+        item = s_item;
+    }
+}
+
 // ---------------- SplitMix64 + Fisher-Yates ----------------
 __device__ __forceinline__ uint64_t sm64_next(uint64_t &s)
 {
@@ -1626,6 +1658,16 @@ const void *kptr()
 
 const void *select_kernel(const KsgVariant &v, bool dx1)
 {
+    if (v.persist) {
+        if (!dx1 || !v.tma) return nullptr;
+        if (v.m == 32 && v.kt == 4)
+            return reinterpret_cast<const void *>(&ksg_lane_persistent_kernel<4, 1, true>);
+        if (v.m == 32 && v.kt == 0)
+            return reinterpret_cast<const void *>(&ksg_lane_persistent_kernel<0, 1, true>);
+        if (v.m == 64 && v.kt == 4)
+            return reinterpret_cast<const void *>(&ksg_lane_persistent_kernel<4, 2, true>);
+        return nullptr;
+    }
     if (dx1 && v.m == 32) {
         if (v.kt == 4)
             return v.tma ? reinterpret_cast<const void *>(&ksg_lane_kernel<4, 1, true>)
@@ -1675,7 +1717,8 @@ cudaError_t ksg_prepare_attributes()
     const KsgVariant vs[] = {{4, 4, QT},  {2, 0, QT},
                              {2, 4, QT},  {32, 4, LW * 32}, {32, 0, LW * 32},
                              {32, 4, LW * 32, true}, {32, 0, LW * 32, true},
-                             {64, 4, LW * 32, true}};
+                             {64, 4, LW * 32, true}, {32, 4, LW * 32, true, true},
+                             {32, 0, LW * 32, true, true}, {64, 4, LW * 32, true, true}};
     for (const auto &v : vs)
         for (int d = 0; d < 2; ++d) {
             const void *f = select_kernel(v, d == 0);
@@ -1738,11 +1781,25 @@ cudaError_t launch_ksg(const KsgLaunch &L, const KsgVariant &v, long long n_item
     if (v.tma && (!lane || !tmap || !L.xval || !L.work || L.jt > LW * 32 || (L.jt & 31)))
         return cudaErrorInvalidValue;
     KsgLaunch arg = L;
+    arg.n_items = n_items;
+    unsigned grid = (unsigned)n_items;
+    if (v.persist != (arg.item_counter != nullptr)) return cudaErrorInvalidValue;
+    if (v.persist) {
+        if (!lane || !arg.work) return cudaErrorInvalidValue;
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, v.qt, smem_bytes);
+        if (e != cudaSuccess) return e;
+        const long long full = (long long)sms * (per_sm > 0 ? per_sm : 1);
+        if (full < n_items) grid = (unsigned)full;
+    }
     CUtensorMap map;
     if (tmap) map = *tmap;
     else std::memset(&map, 0, sizeof map);
     void *args[] = {&arg, &map};
-    return cudaLaunchKernel(f, dim3((unsigned)n_items), dim3(v.qt), args, smem_bytes, st);
+    return cudaLaunchKernel(f, dim3(grid), dim3(v.qt), args, smem_bytes, st);
 }
 
 // One CTA per member row: the member's X values in its group's point order

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "te_runtime.h"
+#include "ksg_tune_table.h"
 
 using namespace teksg;
 
@@ -437,12 +438,30 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
         const bool dx1 = kv.first.dx1, k4 = kv.first.k4;
         auto &gs = kv.second;
         KsgVariant v{4, 4, 128};
+        int tune_jt = 256;
         if (dx1) {
             v = KsgVariant{32, k4 ? 4 : 0, kLaneThreads, true};   // member-lane kernel, TMA tiles
-            // two members per lane when every group has enough members to fill them
+            // tile length and members per lane from the tuning table (or the
+            // context's forced values); two members per lane only when every
+            // group has enough members to fill them
             size_t min_members = SIZE_MAX;
-            for (const HostGroup *g : gs) min_members = std::min(min_members, g->members.size());
-            if (k4 && min_members >= 64) v.m = 64;
+            int tN = 0, tdz = 0;
+            for (const HostGroup *g : gs) {
+                min_members = std::min(min_members, g->members.size());
+                tN = std::max(tN, g->data->T - g->max_lag);
+                tdz = std::max(tdz, (int)g->z.size());
+            }
+            int tune_ms = 1;
+            for (const KsgTuneEntry &e : kKsgTune)
+                if (tN <= e.n_max && tdz <= e.dz_max && min_members >= (size_t)e.min_members) {
+                    tune_jt = e.jt;
+                    tune_ms = e.ms;
+                    break;
+                }
+            if (ctx->opt_jt) tune_jt = ctx->opt_jt;
+            if (ctx->opt_ms) tune_ms = ctx->opt_ms;
+            if (tune_ms == 2 && k4 && min_members >= 64) v.m = 64;
+            v.persist = ctx->opt_persistent != 0;
         } else if (!k4) {
             v = KsgVariant{2, 0, 128};
         } else {
@@ -478,7 +497,7 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
             int maxdyz = 0;
             for (const HostGroup *g : gs)
                 maxdyz = std::max(maxdyz, (int)(g->y.size() + g->z.size()));
-            jt = 256;
+            jt = tune_jt;
             if (maxN < jt) jt = std::max(64, (maxN + 63) & ~63);
             smem = ksg_lane_tma_smem_bytes(maxdyz, jt, v.m);
         } else {
@@ -642,63 +661,98 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
         CK(ksg_prepare_attributes(), "cudaFuncSetAttribute");
         ctx->prepared = 1;
     }
-    if (!ojobs.empty()) {
-        CK(launch_order((const OrderJob *)ctx->ws_ojobs.p, (int)ojobs.size(), ctx->stream),
-           "order launch");
-        ctx->stats.launches++;
-    }
-    if (!cjobs.empty()) {
-        CK(launch_compose((const ComposeJob *)((char *)ctx->ws_ojobs.p + obytes),
-                          (int)cjobs.size(), max_cn, ctx->stream),
-           "compose launch");
-        ctx->stats.launches++;
-    }
-    if (!vjobs.empty()) {
-        CK(launch_value_sort((const ValueSortJob *)((char *)ctx->ws_ojobs.p + obytes + jbytes),
-                             (int)vjobs.size(), ctx->stream),
-           "value sort launch");
-        ctx->stats.launches++;
-    }
-    CK(cudaMemsetAsync(ctx->work_dev, 0, 3 * sizeof(unsigned long long), ctx->stream),
-       "cudaMemsetAsync");
-    CK(cudaEventRecord(ctx->ev_a, ctx->stream), "cudaEventRecord");
-    for (const Plan &p : plans) {
-        KsgLaunch L{};
-        L.groups = (const GroupDesc *)ctx->ws_groups.p + p.g_off;
-        L.n_groups = p.n_groups;
-        L.members = (const MemberDesc *)ctx->ws_members.p + p.m_off;
-        L.cols = (const int *)ctx->ws_cols.p + p.c_off;
-        L.q = ctx->q_dev;
-        L.acc = (unsigned long long *)ctx->ws_acc.p;
-        L.dbg_eps = dbg_eps;
-        L.dbg_nxz = dbg_nxz;
-        L.dbg_nyz = dbg_nyz;
-        L.dbg_nz = dbg_nz;
-        L.dbg_out = dbg_out;
-        L.jt = p.jt;
-        L.work = ctx->work_dev;
-        if (p.v.tma) {
-            L.xval = (const float *)((char *)ctx->ws_xval.p + p.xoff);
-            L.xpitch = p.pitch;
-            CUtensorMap map;
-            CK(encode_xval_map(&map, L.xval, p.pitch, p.rows, p.v.m), "tensor map encode");
-            CK(launch_xval(L, p.rows, ctx->stream), "X-value launch");
+    // The batch's device work.  With the graph option it is captured on the
+    // stream into a CUDA graph, instantiated and launched as one graph (the
+    // timing events then bracket the graph launch).
+    const bool graph = ctx->opt_graph != 0;
+    auto device_work = [&]() -> te_status {
+        if (!ojobs.empty()) {
+            CK(launch_order((const OrderJob *)ctx->ws_ojobs.p, (int)ojobs.size(), ctx->stream),
+               "order launch");
             ctx->stats.launches++;
-            CK(launch_ksg(L, p.v, p.items, p.dx1, p.smem, ctx->stream, &map),
-               "KSG kernel launch");
-        } else {
-            CK(launch_ksg(L, p.v, p.items, p.dx1, p.smem, ctx->stream), "KSG kernel launch");
         }
+        if (!cjobs.empty()) {
+            CK(launch_compose((const ComposeJob *)((char *)ctx->ws_ojobs.p + obytes),
+                              (int)cjobs.size(), max_cn, ctx->stream),
+               "compose launch");
+            ctx->stats.launches++;
+        }
+        if (!vjobs.empty()) {
+            CK(launch_value_sort((const ValueSortJob *)((char *)ctx->ws_ojobs.p + obytes + jbytes),
+                                 (int)vjobs.size(), ctx->stream),
+               "value sort launch");
+            ctx->stats.launches++;
+        }
+        CK(cudaMemsetAsync(ctx->work_dev, 0, 3 * sizeof(unsigned long long), ctx->stream),
+           "cudaMemsetAsync");
+        if (!graph) CK(cudaEventRecord(ctx->ev_a, ctx->stream), "cudaEventRecord");
+        for (const Plan &p : plans) {
+            KsgLaunch L{};
+            L.groups = (const GroupDesc *)ctx->ws_groups.p + p.g_off;
+            L.n_groups = p.n_groups;
+            L.members = (const MemberDesc *)ctx->ws_members.p + p.m_off;
+            L.cols = (const int *)ctx->ws_cols.p + p.c_off;
+            L.q = ctx->q_dev;
+            L.acc = (unsigned long long *)ctx->ws_acc.p;
+            L.dbg_eps = dbg_eps;
+            L.dbg_nxz = dbg_nxz;
+            L.dbg_nyz = dbg_nyz;
+            L.dbg_nz = dbg_nz;
+            L.dbg_out = dbg_out;
+            L.jt = p.jt;
+            L.work = ctx->work_dev;
+            if (p.v.persist) {
+                L.item_counter = ctx->work_dev + 3;
+                CK(cudaMemsetAsync(L.item_counter, 0, sizeof(unsigned long long), ctx->stream),
+                   "cudaMemsetAsync");
+            }
+            if (p.v.tma) {
+                L.xval = (const float *)((char *)ctx->ws_xval.p + p.xoff);
+                L.xpitch = p.pitch;
+                CUtensorMap map;
+                CK(encode_xval_map(&map, L.xval, p.pitch, p.rows, p.v.m), "tensor map encode");
+                CK(launch_xval(L, p.rows, ctx->stream), "X-value launch");
+                ctx->stats.launches++;
+                CK(launch_ksg(L, p.v, p.items, p.dx1, p.smem, ctx->stream, &map),
+                   "KSG kernel launch");
+            } else {
+                CK(launch_ksg(L, p.v, p.items, p.dx1, p.smem, ctx->stream), "KSG kernel launch");
+            }
+            ctx->stats.launches++;
+            ctx->stats.ksg_launches++;
+        }
+        if (!graph) CK(cudaEventRecord(ctx->ev_b, ctx->stream), "cudaEventRecord");
+        CK(copy_d2h(ctx, ctx->work_host, ctx->work_dev, 3 * sizeof(unsigned long long)),
+           "cudaMemcpyAsync");
+        CK(launch_finalize((const unsigned long long *)ctx->ws_acc.p,
+                           (long long *)ctx->ws_keys.p, n_out, ctx->stream),
+           "finalize launch");
         ctx->stats.launches++;
-        ctx->stats.ksg_launches++;
+        return TE_OK;
+    };
+    if (!graph) {
+        if ((st = device_work())) return st;
+    } else {
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal),
+           "cudaStreamBeginCapture");
+        const te_status ws = device_work();
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+        if (ws) {
+            if (g) cudaGraphDestroy(g);
+            return ws;
+        }
+        CK(ce, "cudaStreamEndCapture");
+        cudaGraphExec_t ge = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        CK(ie, "cudaGraphInstantiate");
+        cudaError_t le = cudaEventRecord(ctx->ev_a, ctx->stream);
+        if (le == cudaSuccess) le = cudaGraphLaunch(ge, ctx->stream);
+        if (le == cudaSuccess) le = cudaEventRecord(ctx->ev_b, ctx->stream);
+        cudaGraphExecDestroy(ge);   // released once the launched graph completes
+        CK(le, "cudaGraphLaunch");
     }
-    CK(cudaEventRecord(ctx->ev_b, ctx->stream), "cudaEventRecord");
-    CK(copy_d2h(ctx, ctx->work_host, ctx->work_dev, 3 * sizeof(unsigned long long)),
-       "cudaMemcpyAsync");
-    CK(launch_finalize((const unsigned long long *)ctx->ws_acc.p, (long long *)ctx->ws_keys.p,
-                       n_out, ctx->stream),
-       "finalize launch");
-    ctx->stats.launches++;
     ctx->pend_timed = 1;
     ctx->pend_pair_evals = pair_evals;
     ctx->pend_members = members_total;
@@ -740,7 +794,7 @@ te_status te_ctx_create(int device, te_ctx **out)
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&ctx->ev_a) != cudaSuccess || cudaEventCreate(&ctx->ev_b) != cudaSuccess ||
-        cudaMalloc(&ctx->work_dev, 3 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&ctx->work_dev, 4 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&ctx->work_host, 3 * sizeof(unsigned long long)) != cudaSuccess) {
         te_ctx_destroy(ctx);
         return TE_ECUDA;
@@ -748,6 +802,30 @@ te_status te_ctx_create(int device, te_ctx **out)
     ctx->stream = ctx->own_stream;
     *out = ctx;
     return TE_OK;
+}
+
+te_status te_ctx_set_option(te_ctx *ctx, int32_t option, int64_t value)
+{
+    if (!ctx) return TE_EINVAL;
+    switch (option) {
+    case TE_OPT_KSG_TILE:
+        if (value != 0 && value != 64 && value != 128 && value != 256)
+            return fail(ctx, TE_EINVAL, "the member-lane tile must be 0, 64, 128 or 256 points");
+        ctx->opt_jt = (int)value;
+        return TE_OK;
+    case TE_OPT_KSG_MEMBERS_PER_LANE:
+        if (value < 0 || value > 2)
+            return fail(ctx, TE_EINVAL, "members per lane must be 0, 1 or 2");
+        ctx->opt_ms = (int)value;
+        return TE_OK;
+    case TE_OPT_PERSISTENT:
+    case TE_OPT_GRAPH:
+        if (value != 0 && value != 1) return fail(ctx, TE_EINVAL, "the option takes 0 or 1");
+        (option == TE_OPT_PERSISTENT ? ctx->opt_persistent : ctx->opt_graph) = (int)value;
+        return TE_OK;
+    default:
+        return fail(ctx, TE_EINVAL, "unknown option");
+    }
 }
 
 te_status te_ctx_set_stream(te_ctx *ctx, void *cuda_stream)

@@ -76,7 +76,8 @@ struct te_ctx {
     uint64_t pend_pair_evals = 0, pend_members = 0;
     struct te_server *server = nullptr;   // serving state (te_serve_*), created on demand
     std::mutex serve_start_mu;
-    unsigned long long *work_dev = nullptr;   // KSG kernel work counters [2], error flag [1]
+    unsigned long long *work_dev = nullptr;   // KSG kernel work counters [2], error flag [1],
+                                              // persistent-grid item counter [1]
     unsigned long long *work_host = nullptr;  // pinned copy
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     // second stream for work that overlaps the context's stream (created on
@@ -86,6 +87,9 @@ struct te_ctx {
     int prepared = 0;
     te_trace_fn trace_fn = nullptr;   // te_ctx_set_trace
     void *trace_user = nullptr;
+    // te_ctx_set_option: forced member-lane tile / members per lane (0 = the
+    // tuning table), persistent member-lane grids, batches captured as graphs
+    int opt_jt = 0, opt_ms = 0, opt_persistent = 0, opt_graph = 0;
 };
 
 namespace teksg {
