@@ -55,7 +55,9 @@ typedef struct {
 } te_var;
 
 /* Limits of this build. */
-#define TE_MAX_DIMS 32      /* dx + dy + dz of one estimate */
+#define TE_MAX_DIMS 32      /* dx + dy + dz of one KSG estimate */
+#define TE_GAUSS_MAX_DIMS 40 /* dx + dy + dz of one linear-Gaussian estimate (cmi_gauss,
+                                te_network_infer with estimator 1) */
 #define TE_MAX_K 16         /* nearest neighbours */
 
 /* ---- context and data ---------------------------------------------------- */
@@ -187,7 +189,8 @@ te_status cmi_ksg_batch(te_ctx *ctx, const te_cmi_job *jobs, int32_t n_jobs, dou
  * FP64 Cholesky factors.  Surrogate s permutes the rows of the whole X block
  * with the same permutation cmi_ksg uses (seed, stream_tag, s); Y and Z are
  * never permuted.  params: max_lag, n_surr, seed, stream_tag are used; k and
- * theiler are ignored.  dx <= 8, dx + dy + dz <= TE_MAX_DIMS, N > dx+dy+dz+1.
+ * theiler are ignored.  dx <= 8, dx + dy + dz <= TE_GAUSS_MAX_DIMS (40),
+ * N > dx+dy+dz+1.
  * out_cmi: host double[1 + S]; out_err_bound: NULL or host double[1 + S], a
  * first-order bound on |out_cmi - exact FP64 plug-in value| from the error
  * model of the cross-covariance contraction.
@@ -256,7 +259,7 @@ typedef struct {
     int32_t estimator;             /* 0: KSG (above); 1: the linear-Gaussian estimator of
                                       cmi_gauss (Methods, Vector autoregressive process), k
                                       unused, theiler must be 0, every estimate at most 8 X
-                                      and 32 variables in all; decisions then compare the
+                                      and 40 variables in all; decisions then compare the
                                       FP64 estimates, whose cross-covariances are summed in
                                       float-float or FP64 arithmetic (about 1e-13 relative) */
 } te_infer_params;

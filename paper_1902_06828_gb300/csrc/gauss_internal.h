@@ -6,7 +6,7 @@
 
 namespace teksg {
 
-constexpr int kGaussMaxDims = 32;   // dx + dy + dz
+constexpr int kGaussMaxDims = 40;   // dx + dy + dz
 constexpr int kGaussMaxX = 8;       // dx
 
 // Columns are X (dx), then Y (dy), then Z; W = (Y, Z) has dw = dy + dz
@@ -16,6 +16,18 @@ struct GaussArgs {
     const int *cols;        // [d] device
     int N, S, dx, dy, dw, d;
     const int32_t *perms;   // [S][N] surrogate permutations of the rows of X
+    // the same permutations as 16-bit rows of perm_pitch entries (a multiple
+    // of 8), or nullptr: read by the tensor-core contraction when set
+    const uint16_t *perms16;
+    int perm_pitch;
+    int w0;                 // tensor-core contraction: first W column of this pass (32 per pass)
+    // tensor-core contraction inputs prepared once per call: W's B tiles
+    // (split TF32, core-matrix layout, 8 KB per 32-point chunk and pass) and
+    // the centred X columns in FP32, xcen[i * xcen_pitch + t] (pitch a
+    // multiple of 32); gauss_tc_workspace bytes in all
+    float *btile;
+    float *xcen;
+    int xcen_pitch;
     double *mean;           // [d]
     double *cov;            // [d][d] sample covariance, ddof = 1
     double *LW, *LZ;        // [dw][dw] lower Cholesky factors of S_WW and S_ZZ
@@ -37,9 +49,14 @@ struct GaussArgs {
     int splits, chunks_per_split;
     double *cross_part;
 };
-// splits of the points for (S + 1) * dx rows of N points (fills about two
-// waves of CTAs; every split keeps at least one accumulation group)
+// splits of the points for (S + 1) * dx rows of N points in the batched
+// FP64 / float-float contraction (every split keeps at least one accumulation
+// group)
 int gauss_cross_splits(int rows, int N);
+// splits of the tensor-core contraction: one FP32 accumulation group each
+int gauss_tc_splits(int N);
+// bytes of the tensor-core contraction's prepared inputs (btile, xcen)
+size_t gauss_tc_workspace(int N, int dx, int dw);
 
 cudaError_t gauss_launch_stats(const GaussArgs &A, cudaStream_t st);
 cudaError_t gauss_launch_cross_tc(const GaussArgs &A, cudaStream_t st);

@@ -113,38 +113,48 @@ __device__ __forceinline__ double warp_sum_d(double v)
     return v;
 }
 
-// In-place FP64 Cholesky of an n x n SPD matrix (n <= 32, row-major, lower
-// factor) by one warp: the pivot's sum is a warp reduction, the column below
-// it one row per lane.  False (in every lane) if a pivot is not positive.
+// In-place FP64 Cholesky of an n x n SPD matrix (n <= 64, row-major, lower
+// factor) by one warp: the pivot's sum is a warp reduction of lane-strided
+// partial sums, the column below it one or two rows per lane.  False (in every
+// lane) if a pivot is not positive.
 __device__ bool chol_warp(double *a, int n, int ld)
 {
     const int lane = threadIdx.x & 31;
     for (int j = 0; j < n; ++j) {
-        const double v = lane < j ? a[j * ld + lane] : 0.0;
-        const double s = a[j * ld + j] - warp_sum_d(v * v);
+        double v = 0.0;
+        for (int k = lane; k < j; k += 32) v += a[j * ld + k] * a[j * ld + k];
+        const double s = a[j * ld + j] - warp_sum_d(v);
         if (!(s > 0.0)) return false;
         const double l = sqrt(s);
-        const int i = j + 1 + lane;
-        double t = 0.0;
-        if (i < n) {
-            t = a[i * ld + j];
-            for (int k = 0; k < j; ++k) t -= a[i * ld + k] * a[j * ld + k];
+        double t[2] = {0.0, 0.0};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int i = j + 1 + lane + 32 * h;
+            if (i < n) {
+                t[h] = a[i * ld + j];
+                for (int k = 0; k < j; ++k) t[h] -= a[i * ld + k] * a[j * ld + k];
+            }
         }
         __syncwarp();
-        if (i < n) a[i * ld + j] = t / l;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int i = j + 1 + lane + 32 * h;
+            if (i < n) a[i * ld + j] = t[h] / l;
+        }
         if (lane == 0) a[j * ld + j] = l;
         __syncwarp();
     }
     return true;
 }
 
-// ||L^-1||_F^2 for lower-triangular L (n <= 32) by one warp: lane c solves
-// L x = e_c by forward substitution (x kept in col[c][*], shared memory)
-__device__ double inv_frob2_warp(const double *L, int n, int ld, double (*col)[33])
+// ||L^-1||_F^2 for lower-triangular L (n <= kGaussMaxDims) by one warp: lane
+// c solves L x = e_c for c = lane and lane + 32 by forward substitution (x
+// kept in col[c][*], shared memory)
+__device__ double inv_frob2_warp(const double *L, int n, int ld,
+                                 double (*col)[kGaussMaxDims + 1])
 {
-    const int c = threadIdx.x & 31;
     double s = 0.0;
-    if (c < n) {
+    for (int c = threadIdx.x & 31; c < n; c += 32) {
         for (int i = 0; i < n; ++i) {
             double t = (i == c) ? 1.0 : 0.0;
             for (int k = c; k < i; ++k) t -= L[i * ld + k] * col[c][k];
@@ -164,7 +174,7 @@ __device__ __forceinline__ void gauss_factor_body(const GaussArgs &A)
 {
     // the factorisations run in shared memory (a warp's dependent steps would
     // otherwise wait on global memory) and the factors are written back
-    __shared__ double col[32][33];
+    __shared__ double col[kGaussMaxDims][kGaussMaxDims + 1];
     __shared__ double sW[kGaussMaxDims * kGaussMaxDims], sZ[kGaussMaxDims * kGaussMaxDims];
     if (threadIdx.x >= 32) return;
     const int lane = threadIdx.x;
@@ -256,19 +266,25 @@ __device__ __forceinline__ void gauss_schur_body(const GaussArgs &A, double gamm
 }
 
 // ---------------- tensor-core cross-covariance (tcgen05, split TF32) ----------------
-// D[m][n] = sum_t A[m][t] B[n][t] with A[m][t] = x_i(pi_s(t)) - mean_i (row m =
-// (surrogate s, X dim i)) and B[n][t] = w_n(t) - mean_n (n < dw, zero above).
-// Each operand is split in two TF32 parts, a = a_hi + a_lo (X centred in FP32
-// by its FP64 mean taken as a sum of two floats, W centred in FP64; a_hi =
-// tf32(a), a_lo = tf32(a - a_hi)); the product is a_hi b_hi + a_hi b_lo +
-// a_lo b_hi, three tcgen05.mma.kind::tf32 per K step, FP32 accumulation in
-// tensor memory.  Every kGaussGroup chunks of 32 points the 128 x 32 FP32
-// accumulator is read back (tcgen05.ld) and added to FP64 registers, which
-// bounds the FP32 accumulation error.  One CTA (4 warps) per 128 rows; one
-// thread issues the MMAs, the others stage operands.  Operands use the
-// canonical K-major layout without swizzle: 8-row x 16-byte core matrices,
-// K-adjacent core matrices 128 bytes apart (leading byte offset), 8-row groups
-// 1024 bytes apart (stride byte offset).
+// cross[s][i][n] = sum_t A[(s, i)][t] B[n][t] with A[(s, i)][t] = x_i(pi_s(t))
+// - mean_i (row = (surrogate s, X dim i)) and B[n][t] = w_n(t) - mean_n.  Each
+// operand is split in two TF32 parts, a = a_hi + a_lo (a_hi = tf32(a), a_lo =
+// tf32(a - a_hi)); the product is a_hi b_hi + a_hi b_lo + a_lo b_hi, three
+// tcgen05.mma.kind::tf32 per K step, FP32 accumulation in tensor memory.
+//
+// What does not depend on the surrogate is prepared once per call
+// (gauss_tc_prep_*): W centred in FP64 and split, already laid out as the
+// MMA's B tiles (one 8 KB hi + lo tile per 32-point chunk and 32-column pass),
+// and X centred in FP64 and rounded to FP32 (one rounding of 2^-24).  A CTA
+// owns 128 rows and one FP32 accumulation group of at most kGaussGroup chunks:
+// it copies its B tiles with cp.async.bulk, keeps the X column in shared memory
+// (one X dimension and N <= kGaussColMax) or reads it through L1, gathers each
+// chunk's A operand through the 16-bit permutation rows (loaded one chunk
+// ahead), lets one thread issue the MMAs, and at the end reads the accumulator
+// once (tcgen05.ld) into its FP64 partial-sum row.  Operands use the canonical
+// K-major layout without swizzle: 8-row x 16-byte core matrices, K-adjacent
+// core matrices 128 bytes apart (leading byte offset), 8-row groups 1024 bytes
+// apart (stride byte offset).
 constexpr int kGaussTileM = 128;
 constexpr int kGaussTileN = 32;
 constexpr int kGaussKC = 32;                     // points per chunk (128 bytes of TF32)
@@ -322,23 +338,19 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity)
     return false;
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 {
-    uint32_t r[32];
+    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int a = 0; a < 32; ++a) v[a] = __uint_as_float(r[a]);
+    for (int a = 0; a < 16; ++a) v[a] = __uint_as_float(r[a]);
 }
 
 // byte offset of element (row, k) of a K-major no-swizzle tile with 8 core
@@ -348,28 +360,72 @@ __device__ __forceinline__ uint32_t cm_offset(int row, int k)
     return (uint32_t)(((row >> 3) * 8 + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4);
 }
 
-__global__ void __launch_bounds__(128, 1) gauss_cross_tc_kernel(GaussArgs A)
+constexpr int kGaussColMax = 16384;   // X column points kept in shared memory
+
+// W's B tiles: tile (pass p, chunk c) at btile + (p * nchunks + c) * 2048
+// floats, hi then lo, each in the core-matrix layout of 32 columns x 32 points
+__global__ void gauss_tc_prep_w(GaussArgs A, int nchunks)
 {
-    __shared__ __align__(1024) uint32_t sA_hi[kGaussTileM * kGaussKC];
-    __shared__ __align__(1024) uint32_t sA_lo[kGaussTileM * kGaussKC];
-    __shared__ __align__(1024) uint32_t sB_hi[kGaussTileN * kGaussKC];
-    __shared__ __align__(1024) uint32_t sB_lo[kGaussTileN * kGaussKC];
-    __shared__ __align__(8) unsigned long long s_mbar;
+    const int c = blockIdx.x, pass = blockIdx.y;
+    float *hb = A.btile + ((size_t)pass * nchunks + c) * 2048;
+    float *lb = hb + 1024;
+    for (int e = threadIdx.x; e < kGaussTileN * kGaussKC; e += blockDim.x) {
+        const int n = e / kGaussKC, k = e % kGaussKC;
+        const int t = c * kGaussKC + k, col = pass * kGaussTileN + n;
+        float hi = 0.f, lo = 0.f;
+        if (col < A.dw && t < A.N) {
+            const double v = (double)A.base[A.cols[A.dx + col] + t] - A.mean[A.dx + col];
+            hi = __uint_as_float(to_tf32((float)v));
+            lo = __uint_as_float(to_tf32((float)(v - (double)hi)));
+        }
+        const uint32_t off = cm_offset(n, k) / 4;
+        hb[off] = hi;
+        lb[off] = lo;
+    }
+}
+
+// X centred in FP64, rounded once to FP32: xcen[i * xcen_pitch + t]
+__global__ void gauss_tc_prep_x(GaussArgs A)
+{
+    const int i = blockIdx.y;
+    const float *col = A.base + A.cols[i];
+    const double m = A.mean[i];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < A.xcen_pitch;
+         t += gridDim.x * blockDim.x)
+        A.xcen[(size_t)i * A.xcen_pitch + t] = t < A.N ? (float)((double)col[t] - m) : 0.f;
+}
+
+// 256 threads: thread (half h = tid / 128, row r = tid % 128) stages points
+// 16 h .. 16 h + 15 of every chunk of row r
+template <bool COLSMEM>
+__global__ void __launch_bounds__(256, 2) gauss_cross_tc_kernel(GaussArgs A, int nchunks)
+{
+    extern __shared__ unsigned char gsm_raw[];
+    unsigned char *gsm = gsm_raw + ((1024u - (smem_u32(gsm_raw) & 1023u)) & 1023u);
+    float *sA_hi = reinterpret_cast<float *>(gsm);
+    float *sA_lo = sA_hi + kGaussTileM * kGaussKC;
+    float *sB = sA_lo + kGaussTileM * kGaussKC;          // [kGaussGroup][2][1024]
+    float *scol = sB + kGaussGroup * 2048;               // [xcen_pitch] with COLSMEM
+    __shared__ __align__(8) unsigned long long s_mbar_b, s_mbar_m;
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
 
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int r = tid & (kGaussTileM - 1), half = tid >> 7;
     const int rows = (A.S + 1) * A.dx;
-    const int m = blockIdx.x * kGaussTileM + tid;   // this thread's row
+    const int m = blockIdx.x * kGaussTileM + r;   // this thread's row
     const int split = blockIdx.y;
     const bool mvalid = m < rows;
     const int ms = mvalid ? m / A.dx : 0, mi = mvalid ? m % A.dx : 0;
-    const int32_t *perm = (mvalid && ms > 0) ? A.perms + (size_t)(ms - 1) * A.N : nullptr;
-    const float *cx = A.base + A.cols[mi];
-    // X is centred in FP32 by the FP64 mean as a sum of two floats: two
-    // roundings of 2^-24 relative per value, and no FP64 work per value
-    const double mx = A.mean[mi];
-    const float mx_hi = (float)mx, mx_lo = (float)(mx - (double)mx_hi);
+    const uint16_t *perm16 =
+        (mvalid && ms > 0 && A.perms16) ? A.perms16 + (size_t)(ms - 1) * A.perm_pitch : nullptr;
+    const int32_t *perm32 =
+        (mvalid && ms > 0 && !A.perms16) ? A.perms + (size_t)(ms - 1) * A.N : nullptr;
+    const float *xg = A.xcen + (size_t)mi * A.xcen_pitch;
+    const int w0 = A.w0, pass = w0 / kGaussTileN;
+    const int ch0 = split * A.chunks_per_split;
+    const int nch = min(nchunks, ch0 + A.chunks_per_split) - ch0;   // 1 .. kGaussGroup
+    const uint32_t mbar_b = smem_u32(&s_mbar_b), mbar_m = smem_u32(&s_mbar_m);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -378,9 +434,27 @@ __global__ void __launch_bounds__(128, 1) gauss_cross_tc_kernel(GaussArgs A)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar)));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_b));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_m));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // this group's B tiles: one bulk copy of 8 KB per chunk
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar_b),
+                     "r"((uint32_t)(nch * 8192))
+                     : "memory");
+        for (int c = 0; c < nch; ++c) {
+            const float *src = A.btile + ((size_t)pass * nchunks + ch0 + c) * 2048;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], "
+                "8192, [%2];" ::"r"(smem_u32(sB + c * 2048)),
+                "l"(reinterpret_cast<uint64_t>(src)), "r"(mbar_b)
+                : "memory");
+        }
+    }
+    if (COLSMEM) {   // the (single) X column, centred, into shared memory
+        const float4 *src = reinterpret_cast<const float4 *>(A.xcen);
+        float4 *dst = reinterpret_cast<float4 *>(scol);
+        for (int e = tid; e < A.xcen_pitch / 4; e += 256) dst[e] = __ldg(src + e);
     }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -389,74 +463,58 @@ __global__ void __launch_bounds__(128, 1) gauss_cross_tc_kernel(GaussArgs A)
                            ((uint32_t)(kGaussTileN >> 3) << 17) |
                            ((uint32_t)(kGaussTileM >> 4) << 24);
     const uint32_t aHi = smem_u32(sA_hi), aLo = smem_u32(sA_lo);
-    const uint32_t bHi = smem_u32(sB_hi), bLo = smem_u32(sB_lo);
-    const uint32_t mbar = smem_u32(&s_mbar);
 
-    double acc[kGaussTileN];
-#pragma unroll
-    for (int a = 0; a < kGaussTileN; ++a) acc[a] = 0.0;
+    // permutation entries of this thread's half chunk: 16 indices (-1 past N)
+    uint4 pv[2];
+    auto load_perm = [&](int ch) {
+        const int k0 = ch * kGaussKC + 16 * half;
+        if (perm16) {
+            const uint4 *q = reinterpret_cast<const uint4 *>(perm16 + k0);
+            pv[0] = __ldg(q);
+            pv[1] = __ldg(q + 1);
+        }
+    };
+    auto index_of = [&](int ch, int k) {   // k: 0 .. 15 within the half
+        const int t = ch * kGaussKC + 16 * half + k;
+        if (!mvalid || t >= A.N) return -1;
+        if (perm16) {
+            const uint32_t wv = (&pv[k >> 3].x)[(k >> 1) & 3];
+            return (int)((wv >> (16 * (k & 1))) & 0xFFFFu);
+        }
+        return perm32 ? perm32[t] : t;
+    };
+    load_perm(ch0);
+    // the B tiles have landed, or the copy timed out: decided by the whole CTA
+    bool failed = __syncthreads_or(!mbar_wait(mbar_b, 0)) != 0;
     uint32_t phase = 0;
-    const int nchunks_all = (A.N + kGaussKC - 1) / kGaussKC;
-    const int ch0 = split * A.chunks_per_split;
-    const int ch1 = min(nchunks_all, ch0 + A.chunks_per_split);
-    bool failed = false;
-
-    for (int ch = ch0; ch < ch1 && !failed; ++ch) {
-        const int k0 = ch * kGaussKC;
-        // stage A: this thread's row, 32 points, 16 at a time: all permutation
-        // entries, then all values, are loaded before any is used
+    for (int c = 0; c < nch && !failed; ++c) {
+        const int ch = ch0 + c;
+        // stage A: this thread's half of its row's chunk, all gathers before any use
         {
             unsigned char *hb = reinterpret_cast<unsigned char *>(sA_hi);
             unsigned char *lb = reinterpret_cast<unsigned char *>(sA_lo);
+            float xv[16];
 #pragma unroll
-            for (int h16 = 0; h16 < kGaussKC; h16 += 16) {
-                int tx[16];
-                float xv[16];
-#pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const int t = k0 + h16 + k;
-                    tx[k] = (mvalid && t < A.N) ? (perm ? perm[t] : t) : -1;
-                }
-#pragma unroll
-                for (int k = 0; k < 16; ++k) xv[k] = tx[k] >= 0 ? cx[tx[k]] : 0.f;
-#pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    float hi = 0.f, lo = 0.f;
-                    if (tx[k] >= 0) {
-                        const float v = __fsub_rn(__fsub_rn(xv[k], mx_hi), mx_lo);
-                        hi = __uint_as_float(to_tf32(v));
-                        lo = __uint_as_float(to_tf32(__fsub_rn(v, hi)));   // v - hi is exact
-                    }
-                    const uint32_t off = cm_offset(tid, h16 + k);
-                    *reinterpret_cast<float *>(hb + off) = hi;
-                    *reinterpret_cast<float *>(lb + off) = lo;
-                }
+            for (int k = 0; k < 16; ++k) {
+                const int idx = index_of(ch, k);
+                xv[k] = idx < 0 ? 0.f : (COLSMEM ? scol[idx] : __ldg(xg + idx));
             }
-        }
-        // stage B: 32 rows x 32 points, 8 values per thread
-        {
-            unsigned char *hb = reinterpret_cast<unsigned char *>(sB_hi);
-            unsigned char *lb = reinterpret_cast<unsigned char *>(sB_lo);
-            for (int e = tid; e < kGaussTileN * kGaussKC; e += 128) {
-                const int n = e / kGaussKC, k = e % kGaussKC;
-                const int t = k0 + k;
-                float hi = 0.f, lo = 0.f;
-                if (n < A.dw && t < A.N) {
-                    const double v = (double)A.base[A.cols[A.dx + n] + t] - A.mean[A.dx + n];
-                    hi = __uint_as_float(to_tf32((float)v));
-                    lo = __uint_as_float(to_tf32((float)(v - (double)hi)));
-                }
-                const uint32_t off = cm_offset(n, k);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const float hi = __uint_as_float(to_tf32(xv[k]));
+                const float lo = __uint_as_float(to_tf32(__fsub_rn(xv[k], hi)));
+                const uint32_t off = cm_offset(r, 16 * half + k);
                 *reinterpret_cast<float *>(hb + off) = hi;
                 *reinterpret_cast<float *>(lb + off) = lo;
             }
         }
+        if (c + 1 < nch) load_perm(ch + 1);   // in flight while the MMAs run
         // generic-proxy smem writes -> visible to the tensor core (async proxy)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const bool first = ((ch - ch0) % kGaussGroup) == 0;
+            const uint32_t bHi = smem_u32(sB + c * 2048), bLo = bHi + 4096;
 #pragma unroll
             for (int q = 0; q < kGaussKC / 8; ++q) {   // K = 8 TF32 per MMA
                 const uint32_t ko = q * 256;            // two core matrices along K
@@ -464,45 +522,39 @@ __global__ void __launch_bounds__(128, 1) gauss_cross_tc_kernel(GaussArgs A)
                 const uint64_t dAl = smem_desc(aLo + ko, 128, 1024);
                 const uint64_t dBh = smem_desc(bHi + ko, 128, 1024);
                 const uint64_t dBl = smem_desc(bLo + ko, 128, 1024);
-                mma_tf32(tmem, dAh, dBh, idesc, (first && q == 0) ? 0u : 1u);
+                mma_tf32(tmem, dAh, dBh, idesc, (c == 0 && q == 0) ? 0u : 1u);
                 mma_tf32(tmem, dAh, dBl, idesc, 1u);
                 mma_tf32(tmem, dAl, dBh, idesc, 1u);
             }
             asm volatile(
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    mbar)
+                    mbar_m)
                 : "memory");
         }
-        // every thread waits: the MMAs have read the smem tiles (and, at a
-        // group end, written the accumulator) before they are reused
-        if (!mbar_wait(mbar, phase)) atomicExch(&s_fail, 1);
+        // every thread waits: the MMAs have read the A tile before it is
+        // restaged (and, after the last chunk, written the accumulator)
+        if (!mbar_wait(mbar_m, phase)) atomicExch(&s_fail, 1);
+        phase ^= 1u;
         __syncthreads();
         if (s_fail) {
-            // give the in-flight MMAs a second bounded wait before the
-            // accumulator is freed; report the failure either way
-            mbar_wait(mbar, phase);
+            mbar_wait(mbar_m, phase ^ 1u);   // a second bounded wait before TMEM is freed
             failed = true;
-            break;
         }
-        phase ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const bool group_end = ((ch - ch0) % kGaussGroup) == kGaussGroup - 1 || ch == ch1 - 1;
-        if (group_end) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
-#pragma unroll
-            for (int a = 0; a < kGaussTileN; ++a) acc[a] += (double)v[a];
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        }
-        __syncthreads();
     }
     if (failed && tid == 0) atomicExch(A.status + 1, 1);
-    if (!failed && mvalid) {
-        double *part = A.cross_part + ((size_t)split * rows + m) * A.dw;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!failed) {
+        // warps w and w + 4 share TMEM lanes 32 (w % 4) ..; each reads 16 columns
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + 16u * half, v);
+        if (mvalid) {
+            double *part = A.cross_part + ((size_t)split * rows + m) * A.dw + w0 + 16 * half;
 #pragma unroll
-        for (int n = 0; n < kGaussTileN; ++n)
-            if (n < A.dw) part[n] = acc[n];
+            for (int n = 0; n < 16; ++n)
+                if (w0 + 16 * half + n < A.dw) part[n] = (double)v[n];
+        }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -682,7 +734,11 @@ __device__ __forceinline__ void gauss_cross_f64_any(const GaussArgs &A, int bx, 
     case 13: gauss_cross_f64_body<26>(A, bx, by, sW); break;
     case 14: gauss_cross_f64_body<28>(A, bx, by, sW); break;
     case 15: gauss_cross_f64_body<30>(A, bx, by, sW); break;
-    default: gauss_cross_f64_body<32>(A, bx, by, sW); break;
+    case 16: gauss_cross_f64_body<32>(A, bx, by, sW); break;
+    case 17: gauss_cross_f64_body<34>(A, bx, by, sW); break;
+    case 18: gauss_cross_f64_body<36>(A, bx, by, sW); break;
+    case 19: gauss_cross_f64_body<38>(A, bx, by, sW); break;
+    default: gauss_cross_f64_body<40>(A, bx, by, sW); break;
     }
 }
 
@@ -809,9 +865,16 @@ cudaError_t gauss_launch_keys(const double *v, int n, long long *keys, int *bad,
 
 int gauss_cross_splits(int rows, int N)
 {
+    // enough CTAs for four resident per SM (each split ends in an FP64
+    // partial-sum row that the reduction adds); the SM count is the device's
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms < 1)
+        sms = 1;
     const int tiles = (rows + kGaussTileM - 1) / kGaussTileM;
     const int groups = (N + kGaussKC * kGaussGroup - 1) / (kGaussKC * kGaussGroup);
-    int splits = (2 * 152 + tiles - 1) / tiles;
+    int splits = (4 * sms + tiles - 1) / tiles;
     return splits < 1 ? 1 : (splits > groups ? groups : splits);
 }
 
@@ -827,14 +890,61 @@ cudaError_t gauss_launch_stats(const GaussArgs &A, cudaStream_t st)
     return cudaGetLastError();
 }
 
+size_t gauss_tc_workspace(int N, int dx, int dw)
+{
+    const size_t nchunks = (size_t)(N + kGaussKC - 1) / kGaussKC;
+    const size_t passes = (size_t)(dw + kGaussTileN - 1) / kGaussTileN;
+    const size_t pitch = ((size_t)N + 31) & ~(size_t)31;
+    return passes * nchunks * 2048 * 4 + (size_t)dx * pitch * 4;
+}
+
+int gauss_tc_splits(int N)
+{
+    const int nchunks = (N + kGaussKC - 1) / kGaussKC;
+    return (nchunks + kGaussGroup - 1) / kGaussGroup;
+}
+
 cudaError_t gauss_launch_cross_tc(const GaussArgs &A, cudaStream_t st)
 {
     const int rows = (A.S + 1) * A.dx;
-    if (A.splits < 1 || A.splits > 65535) return cudaErrorInvalidValue;
-    gauss_cross_tc_kernel<<<dim3((rows + kGaussTileM - 1) / kGaussTileM, A.splits), 128, 0, st>>>(
-        A);
+    const int nchunks = (A.N + kGaussKC - 1) / kGaussKC;
+    if (A.splits < 1 || A.splits > 65535 || A.chunks_per_split > kGaussGroup || !A.btile ||
+        !A.xcen || (A.xcen_pitch & 31) || A.xcen_pitch < A.N ||
+        (reinterpret_cast<uintptr_t>(A.btile) & 15) || (reinterpret_cast<uintptr_t>(A.xcen) & 15))
+        return cudaErrorInvalidValue;
+    if (A.perms16 && (A.perm_pitch < A.N || (A.perm_pitch & 7) ||
+                      (reinterpret_cast<uintptr_t>(A.perms16) & 15)))
+        return cudaErrorInvalidValue;
+    const int passes = (A.dw + kGaussTileN - 1) / kGaussTileN;
+    gauss_tc_prep_w<<<dim3(nchunks, passes), 256, 0, st>>>(A, nchunks);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    gauss_tc_prep_x<<<dim3((A.xcen_pitch + 255) / 256, A.dx), 256, 0, st>>>(A);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const bool colsmem = A.dx == 1 && A.xcen_pitch <= kGaussColMax;
+    const size_t smem = 1024 + (size_t)4 * (2 * kGaussTileM * kGaussKC + kGaussGroup * 2048 +
+                                            (colsmem ? A.xcen_pitch : 0));
+    const void *f = colsmem ? reinterpret_cast<const void *>(&gauss_cross_tc_kernel<true>)
+                            : reinterpret_cast<const void *>(&gauss_cross_tc_kernel<false>);
+    static bool attr_done[64][2] = {};
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && !attr_done[dev][colsmem]) {
+        if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      200 * 1024)) != cudaSuccess)
+            return e;
+        attr_done[dev][colsmem] = true;
+    }
+    // W wider than one 32-column tile: one pass per 32 columns
+    for (int w0 = 0; w0 < A.dw; w0 += kGaussTileN) {
+        GaussArgs P = A;
+        P.w0 = w0;
+        int nc = nchunks;
+        void *args[] = {&P, &nc};
+        e = cudaLaunchKernel(f, dim3((rows + kGaussTileM - 1) / kGaussTileM, A.splits), dim3(256),
+                             args, smem, st);
+        if (e != cudaSuccess) return e;
+    }
     const long long total = (long long)rows * A.dw;
     gauss_cross_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(A);
     return cudaGetLastError();
@@ -842,7 +952,8 @@ cudaError_t gauss_launch_cross_tc(const GaussArgs &A, cudaStream_t st)
 
 double gauss_tc_gamma()
 {
-    // split products: 3 * 2^-22 relative; FP32 centring of X: 2 * 2^-24;
+    // split products: 3 * 2^-22 relative; FP32 rounding of the centred X (one,
+    // counted twice);
     // FP32 accumulation of at most 3 * kGaussKC * kGaussGroup products per
     // group, 2^-23 per addition
     return 3.0 * std::ldexp(1.0, -22) + 2.0 * std::ldexp(1.0, -24) +

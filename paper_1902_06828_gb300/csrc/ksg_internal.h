@@ -165,6 +165,14 @@ cudaError_t launch_perms(int32_t *out, long long stride, int n, uint64_t seed, u
                          uint64_t stage, uint64_t iter, uint64_t s_first, int n_perm,
                          cudaStream_t st);
 
+// The same permutations as launch_perms for n <= kPerm16MaxN, as 16-bit rows of
+// `pitch` entries (pitch a multiple of 8 and >= n, zeros past n; out 16-byte
+// aligned): permutation s - s_first at out + (s - s_first) * pitch.
+constexpr int kPerm16MaxN = 65535;
+cudaError_t launch_perms16(uint16_t *out, int pitch, int n, uint64_t seed, uint64_t target,
+                           uint64_t stage, uint64_t iter, uint64_t s_first, int n_perm,
+                           cudaStream_t st);
+
 // Surrogates of R pooled trials of n points (R * n ints per surrogate, n_perm
 // of them at out): mode 0 shuffles the trial order, mode 1 the points inside
 // each trial, keyed like launch_perms.

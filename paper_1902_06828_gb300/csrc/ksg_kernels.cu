@@ -1374,6 +1374,81 @@ __device__ void fy_shuffle16(uint16_t *p, int n, uint64_t st, int32_t *out)
     for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = (int32_t)p[i];
 }
 
+// One round of fy_shuffle16's warp walk for a permutation p (state: the top
+// step hi and this lane's draw jc).  Called by the whole warp while hi >= 1.
+__device__ __forceinline__ void fy16_round(uint16_t *p, int n, uint64_t st, int &hi, int &jc)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lower = (1u << lane) - 1u;
+    const int i = hi - lane;
+    const bool valid = i >= 1;
+    const int j = valid ? jc : -1 - lane;   // invalid lanes: distinct dummies
+    const int is = hi - 32 - lane;
+    const int js = is >= 1 ? fy_draw(st, n, is) : 0;
+    int lim = !valid ? 0 : (j == i ? 32 : hi - j);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(full, lim, o);
+        if (lane >= o) lim = min(lim, t);
+    }
+    const unsigned same = __match_any_sync(full, j);
+    const unsigned run = __ballot_sync(full, valid && lane < lim && (same & lower) == 0);
+    const int k = run == full ? 32 : __ffs(~run) - 1;   // >= 1: step hi always applies
+    const bool act = lane < k && j != i;
+    uint16_t a = 0, b = 0;
+    if (act) {
+        a = p[i];
+        b = p[j];
+    }
+    __syncwarp();
+    if (act) {
+        p[i] = b;
+        p[j] = a;
+    }
+    __syncwarp();
+    const int from_cur = __shfl_down_sync(full, j, k & 31);
+    const int from_ahead = __shfl_sync(full, js, (lane + k - 32) & 31);
+    jc = lane < 32 - k ? from_cur : from_ahead;
+    hi -= k;
+}
+
+// The same permutations as fisher_yates_kernel (16-bit mode), written as
+// 16-bit rows of `pitch` entries (a multiple of 8, zeros past n): one warp per
+// permutation, the rounds of fy_shuffle16.  (Two walks interleaved in one warp
+// were measured 1.5x slower: the rounds' warp collectives and __syncwarp keep
+// the two chains from overlapping, and half as many warps remain.)
+__global__ void fisher_yates16_kernel(uint16_t *out, int pitch, int n, uint64_t seed,
+                                      uint64_t target, uint64_t stage, uint64_t iter,
+                                      uint64_t s_first)
+{
+    extern __shared__ int32_t sperm16[];
+    uint16_t *p = reinterpret_cast<uint16_t *>(sperm16);
+    uint64_t h = sm64_once(seed ^ target);
+    h = sm64_once(h ^ stage);
+    h = sm64_once(h ^ iter);
+    const uint64_t st = sm64_once(h ^ (s_first + blockIdx.x));
+    for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = (uint16_t)i;
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    int hi = n - 1;
+    int jc = (hi - lane >= 1) ? fy_draw(st, n, hi - lane) : 0;
+    while (hi >= 1) fy16_round(p, n, st, hi, jc);
+    __syncwarp();
+    uint16_t *o = out + (long long)blockIdx.x * pitch;
+    for (int i = 8 * threadIdx.x; i < pitch; i += 8 * blockDim.x) {
+        uint16_t v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = i + u < n ? p[i + u] : (uint16_t)0;
+        uint4 w;
+        w.x = v[0] | ((uint32_t)v[1] << 16);
+        w.y = v[2] | ((uint32_t)v[3] << 16);
+        w.z = v[4] | ((uint32_t)v[5] << 16);
+        w.w = v[6] | ((uint32_t)v[7] << 16);
+        *reinterpret_cast<uint4 *>(o + i) = w;
+    }
+}
+
 // in_smem: bit 0 = the permutation is built in shared memory, bit 1 = the
 // draws are computed in parallel into shared memory after it, 4 = the
 // permutation as 16-bit values with the draws computed by the swapping warp
@@ -1896,6 +1971,26 @@ cudaError_t launch_perms(int32_t *out, long long stride, int n, uint64_t seed, u
     }
     fisher_yates_kernel<<<n_perm, threads, bytes, st>>>(out, stride, n, seed, target, stage,
                                                         iter, s_first, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_perms16(uint16_t *out, int pitch, int n, uint64_t seed, uint64_t target,
+                           uint64_t stage, uint64_t iter, uint64_t s_first, int n_perm,
+                           cudaStream_t st)
+{
+    if (n_perm <= 0) return cudaSuccess;
+    if (n < 1 || n > kPerm16MaxN || pitch < n || (pitch & 7) ||
+        (reinterpret_cast<uintptr_t>(out) & 15))
+        return cudaErrorInvalidValue;
+    static bool attr_done[kAttrDevices] = {};
+    {
+        const cudaError_t e =
+            smem_attr_once(reinterpret_cast<const void *>(&fisher_yates16_kernel),
+                           200 * 1024, attr_done);
+        if (e != cudaSuccess) return e;
+    }
+    fisher_yates16_kernel<<<n_perm, 32, (size_t)n * 2, st>>>(out, pitch, n, seed, target, stage,
+                                                            iter, s_first);
     return cudaGetLastError();
 }
 

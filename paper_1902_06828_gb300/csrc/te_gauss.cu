@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "gauss_internal.h"
+#include "ksg_internal.h"
 #include "te_runtime.h"
 
 using namespace teksg;
@@ -99,7 +100,8 @@ te_status run_groups_gauss(te_ctx *ctx, const std::vector<HostGroup> &groups, in
         const int N = g.data->T - g.max_lag;
         const int dy = (int)g.y.size(), dz = (int)g.z.size();
         if (g.dx > kGaussMaxX || g.dx + dy + dz > kGaussMaxDims)
-            return fail(ctx, TE_EINVAL, "the Gaussian estimator takes dx <= 8 and dx + dy + dz <= 32");
+            return fail(ctx, TE_EINVAL,
+                        "the Gaussian estimator takes dx <= 8 and dx + dy + dz <= 40");
         if (N <= g.dx + dy + dz + 1)
             return fail(ctx, TE_EINVAL, "need more points than variables + 1");
         std::map<int, std::vector<const HostMember *>> by;
@@ -221,7 +223,7 @@ extern "C" te_status cmi_gauss(te_ctx *ctx, const te_data *data, const te_var *x
         te_status st;
         if (!p || !out_cmi) return fail(ctx, TE_EINVAL, "params or out_cmi is NULL");
         if ((st = validate_estimate(ctx, data, x, dx, y, dy, z, dz, 1, 0, p->max_lag,
-                                    p->n_surr)))
+                                    p->n_surr, TE_GAUSS_MAX_DIMS)))
             return st;
         if (dx > kGaussMaxX) return fail(ctx, TE_EINVAL, "cmi_gauss supports dx <= 8");
         const int N = data->T - p->max_lag, S = p->n_surr;
@@ -230,14 +232,31 @@ extern "C" te_status cmi_gauss(te_ctx *ctx, const te_data *data, const te_var *x
         CK(cudaSetDevice(ctx->device), "cudaSetDevice");
         // workspace: the estimate's doubles, its estimates and bounds, then ints
         GaussArgs A{};
-        const size_t ws = gauss_shape(A, N, S, dx, dy, dz, gauss_cross_splits((S + 1) * dx, N));
+        const size_t ws = gauss_shape(A, N, S, dx, dy, dz, gauss_tc_splits(N));
         const size_t nd = ws + 2 * (size_t)(S + 1);
         if ((st = ensure_dev(ctx, ctx->ws_gauss, nd * 8 + (size_t)(d + 8) * 4))) return st;
-        if ((st = ensure_dev(ctx, ctx->ws_perm, (size_t)std::max(S, 1) * N * 4))) return st;
+        // permutations as 16-bit rows (pitch a multiple of 8 entries) when the
+        // points allow: half the bytes for Fisher-Yates to write and the
+        // contraction to read, which reads its rows with 16-byte loads
+        const bool p16 = N <= kPerm16MaxN;
+        const int pitch16 = (N + 7) & ~7;
+        const size_t perm_bytes =
+            p16 ? (size_t)std::max(S, 1) * pitch16 * 2 : (size_t)std::max(S, 1) * N * 4;
+        if ((st = ensure_dev(ctx, ctx->ws_perm, perm_bytes))) return st;
         double *w = (double *)ctx->ws_gauss.p;
         gauss_bind(A, w);
         A.base = data->d_series;
-        A.perms = (const int32_t *)ctx->ws_perm.p;
+        A.perms = p16 ? nullptr : (const int32_t *)ctx->ws_perm.p;
+        A.perms16 = p16 ? (const uint16_t *)ctx->ws_perm.p : nullptr;
+        A.perm_pitch = p16 ? pitch16 : 0;
+        if ((st = ensure_dev(ctx, ctx->ws_gtile, gauss_tc_workspace(N, dx, dy + dz)))) return st;
+        {
+            const size_t nchunks = (size_t)(N + 31) / 32;
+            const size_t passes = (size_t)(dy + dz + 31) / 32;
+            A.btile = (float *)ctx->ws_gtile.p;
+            A.xcen = A.btile + passes * nchunks * 2048;
+            A.xcen_pitch = (N + 31) & ~31;
+        }
         A.out = w + ws;
         A.err = A.out + (S + 1);
         int *ip = (int *)(w + nd);
@@ -258,9 +277,14 @@ extern "C" te_status cmi_gauss(te_ctx *ctx, const te_data *data, const te_var *x
         CK(cudaStreamWaitEvent(ctx->aux_stream, ctx->ev_fork, 0), "cudaStreamWaitEvent");
         CK(gauss_launch_stats(A, ctx->aux_stream), "Gaussian statistics launch");
         CK(cudaEventRecord(ctx->ev_join, ctx->aux_stream), "cudaEventRecord");
-        CK(launch_perms((int32_t *)ctx->ws_perm.p, N, N, p->seed, p->stream_tag, 0, 0, 1, S,
-                        ctx->stream),
-           "permutation launch");
+        if (p16)
+            CK(launch_perms16((uint16_t *)ctx->ws_perm.p, pitch16, N, p->seed, p->stream_tag, 0,
+                              0, 1, S, ctx->stream),
+               "permutation launch");
+        else
+            CK(launch_perms((int32_t *)ctx->ws_perm.p, N, N, p->seed, p->stream_tag, 0, 0, 1, S,
+                            ctx->stream),
+               "permutation launch");
         CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0), "cudaStreamWaitEvent");
         CK(gauss_launch_cross_tc(A, ctx->stream), "tensor-core cross-covariance launch");
         const double gamma = gauss_tc_gamma();

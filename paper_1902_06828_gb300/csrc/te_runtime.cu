@@ -220,15 +220,15 @@ double key_to_cmi(const te_ctx *ctx, int64_t hi, uint64_t lo, int k, int N)
 
 te_status check_estimate(const te_ctx *ctx, const te_data *data, const te_var *x, int dx,
                          const te_var *y, int dy, const te_var *z, int dz, int k, int theiler,
-                         int max_lag, int n_surr, std::string &msg)
+                         int max_lag, int n_surr, std::string &msg, int max_dims)
 {
     if (!data) return (msg = "data is NULL", TE_EINVAL);
     if (data->ctx != ctx) return (msg = "data belongs to another context", TE_EINVAL);
     if (!x || dx < 1) return (msg = "x needs at least one variable", TE_EINVAL);
     if (!y || dy < 1) return (msg = "y needs at least one variable", TE_EINVAL);
     if (dz < 0 || (dz > 0 && !z)) return (msg = "z is NULL with dz > 0", TE_EINVAL);
-    if (dx + dy + dz > TE_MAX_DIMS)
-        return (msg = "dx + dy + dz exceeds TE_MAX_DIMS (32)", TE_EINVAL);
+    if (dx + dy + dz > max_dims)
+        return (msg = "dx + dy + dz exceeds " + std::to_string(max_dims), TE_EINVAL);
     if (k < 1 || k > TE_MAX_K) return (msg = "k must be in 1..16", TE_EINVAL);
     if (theiler < 0) return (msg = "theiler window must be >= 0", TE_EINVAL);
     if (n_surr < 0) return (msg = "n_surr must be >= 0", TE_EINVAL);
@@ -253,11 +253,11 @@ te_status check_estimate(const te_ctx *ctx, const te_data *data, const te_var *x
 
 te_status validate_estimate(te_ctx *ctx, const te_data *data, const te_var *x, int dx,
                             const te_var *y, int dy, const te_var *z, int dz, int k, int theiler,
-                            int max_lag, int n_surr)
+                            int max_lag, int n_surr, int max_dims)
 {
     std::string msg;
-    const te_status st =
-        check_estimate(ctx, data, x, dx, y, dy, z, dz, k, theiler, max_lag, n_surr, msg);
+    const te_status st = check_estimate(ctx, data, x, dx, y, dy, z, dz, k, theiler, max_lag,
+                                        n_surr, msg, max_dims);
     if (st) ctx->err = msg;
     return st;
 }
@@ -846,7 +846,7 @@ void te_ctx_destroy(te_ctx *ctx)
     DevBuf *bufs[] = {&ctx->ws_groups, &ctx->ws_members, &ctx->ws_cols,  &ctx->ws_acc,
                       &ctx->ws_keys,   &ctx->ws_perm,    &ctx->ws_stat,  &ctx->ws_dbg,
                       &ctx->ws_order,  &ctx->ws_ojobs,  &ctx->ws_cperm, &ctx->ws_gauss,
-                      &ctx->ws_vsort,  &ctx->ws_xval};
+                      &ctx->ws_vsort,  &ctx->ws_xval,   &ctx->ws_gtile};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->q_dev) cudaFree(ctx->q_dev);

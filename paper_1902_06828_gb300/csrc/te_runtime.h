@@ -67,6 +67,7 @@ struct te_ctx {
     teksg::DevBuf ws_groups, ws_members, ws_cols, ws_acc, ws_keys, ws_perm, ws_stat, ws_dbg;
     teksg::DevBuf ws_order, ws_ojobs, ws_cperm, ws_gauss, ws_vsort;
     teksg::DevBuf ws_xval;   // X-value rows of the TMA-staged lane kernel
+    teksg::DevBuf ws_gtile;  // cmi_gauss: the contraction's prepared B tiles and centred X
     // pinned host staging
     void *pin = nullptr;
     size_t pin_cap = 0;
@@ -119,12 +120,14 @@ cudaError_t copy_d2h(te_ctx *ctx, void *dst, const void *src, size_t bytes);
 
 // Validate one estimate's variables against its data and parameters: the pure
 // form reports through msg (safe from any thread); the other sets ctx->err.
+// max_dims: TE_MAX_DIMS for the KSG estimator, TE_GAUSS_MAX_DIMS for the
+// linear-Gaussian one.
 te_status check_estimate(const te_ctx *ctx, const te_data *data, const te_var *x, int dx,
                          const te_var *y, int dy, const te_var *z, int dz, int k, int theiler,
-                         int max_lag, int n_surr, std::string &msg);
+                         int max_lag, int n_surr, std::string &msg, int max_dims = TE_MAX_DIMS);
 te_status validate_estimate(te_ctx *ctx, const te_data *data, const te_var *x, int dx,
                             const te_var *y, int dy, const te_var *z, int dz, int k, int theiler,
-                            int max_lag, int n_surr);
+                            int max_lag, int n_surr, int max_dims = TE_MAX_DIMS);
 
 // Run every group in fused launches; keys of all n_out slots end up in
 // ctx->ws_keys as int64 pairs (hi, lo).  Slots not written by any member are 0.

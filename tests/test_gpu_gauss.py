@@ -24,10 +24,21 @@ CASES = [
     ("chain3", [(0, 1), (1, 1), (1, 2)], [(2, 0)], [(2, 1)], 2, 20),            # dx = 3
     ("var10", [(3, 2)], [(0, 0)], [(0, 1), (0, 2), (4, 1)], 5, 100),
     ("var10", [(9, 2)], [(0, 0), (1, 0)], [(0, 1)] + [(q, 1) for q in range(2, 9)], 5, 40),
-    # the limits: dx = 8 and 32 variables in all
+    # dx = 8 and 32 variables in all
     ("var10", [(q, 1) for q in range(1, 9)], [(0, 0)],
      [(0, l) for l in range(1, 6)] + [(q, l) for q in range(1, 9) for l in (2, 3)] + [(9, 1), (9, 2)],
      5, 30),
+    # past 32: W of 33 columns (the contraction's second 32-column pass holds
+    # one), W of 39 (d = 40, the limit), and dx = 8 with 40 variables in all
+    ("var10", [(9, 3)], [(0, 0)],
+     [(0, l) for l in range(1, 6)] + [(q, l) for q in range(1, 9) for l in (1, 2, 3, 4)][:27],
+     5, 25),
+    ("var10", [(9, 3)], [(0, 0)],
+     [(0, l) for l in range(1, 6)] + [(q, l) for q in range(1, 9) for l in (1, 2, 4, 5)] + [(9, 1)],
+     5, 25),
+    ("var10", [(q, 1) for q in range(1, 9)], [(0, 0)],
+     [(0, l) for l in range(1, 6)] + [(q, l) for q in range(1, 9) for l in (2, 3, 4)] + [(9, 2), (9, 3)],
+     5, 20),
 ]
 
 
@@ -52,6 +63,15 @@ def test_gauss_matches_oracle_within_reported_bound(env, wl, x, y, z, ml, S):
     # relative.  The other cases stay at or below 9.1e-8.  2.5e-7 allows 2.5x
     # that worst case.
     assert np.max(np.abs(got - want)) < 2.5e-7
+
+
+def test_gauss_dimension_limit(env):
+    te, ctx = env
+    s = synth.workload_var10(T=3000, seed=1)["series"]
+    data = te.te_data_create(ctx, s)
+    z = [(q, l) for q in range(1, 9) for l in range(1, 6)][:39]   # 41 variables with x, y
+    with pytest.raises(te.TEError, match="TE_EINVAL"):
+        te.cmi_gauss(ctx, data, [(9, 1)], [(0, 0)], z, max_lag=5, n_surr=3)
 
 
 def test_gauss_singular_conditioning_rejected(env):
