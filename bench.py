@@ -265,6 +265,7 @@ def run_serve(args):
                       "estimates_per_s": est / span, "requests_per_s": nreq / span})
     st = te.te_serve_get_stats(ctx)
     te.te_serve_stop(ctx)
+    greedy = serve_greedy(te, seconds=args.serve_seconds)
     # plain path on the same mix: one call per estimate, no surrogates batched
     plain = [request(5000 + i) for i in range(max(20, nreq // 4))]
     te.cmi_ksg(ctx, plain[0].data, plain[0].x, plain[0].y, plain[0].z, k=4, max_lag=5)
@@ -281,8 +282,73 @@ def run_serve(args):
                        "max_inflight": 2, "max_batch_jobs": 256, "budget_GiB": 16},
             "rates": rates, "plain_path_estimates_per_s": plain_rate,
             "served_over_plain": best / plain_rate, "batches": st["batches"],
-            "peak_admitted_bytes": st["peak_bytes"]}
+            "peak_admitted_bytes": st["peak_bytes"], "greedy_loops": greedy}
     print(json.dumps(line), flush=True)
+
+
+def serve_greedy(te, seconds=15.0, n_loops=100, plain_calls=40):
+    """Serving fed by greedy loops: n_loops concurrent target loops (each one
+    target's greedy inference, every test one request of one job per
+    candidate with the loop's S surrogates) over 6 data sets of 10 processes
+    (coupled logistic maps and VAR, T = 1000, 3000, 10000), S ~ U{100..1000}
+    per loop, joint dims growing with the selections, one server.  The loops
+    run for `seconds` after a warm-up; the line reports request latency
+    (submit of a test's jobs to its last result) and estimates/s over the
+    completed requests, and the plain path (one cmi_ksg call per estimate, no
+    surrogates) on a sample of the served jobs."""
+    import synth
+    from paper_1902_06828_gb300.serve_loops import TargetLoop, run_served
+    rng = np.random.default_rng(7)
+    ctx = te.Context(0)
+    sets = []
+    for kind, T, seed in (("clm", 1000, 11), ("var", 1000, 12), ("clm", 3000, 13),
+                          ("var", 3000, 14), ("clm", 10000, 15), ("var", 10000, 16)):
+        x = (synth.clm_er(n=10, T=T, seed=seed)[0] if kind == "clm"
+             else synth.var_er(n=10, p=0.3, T=T, seed=seed)[0])
+        sets.append((te.te_data_create(ctx, synth.standardise_jitter(x, seed)), kind, T))
+
+    def make(i, tag0):
+        d, kind, T = sets[i % len(sets)]
+        return TargetLoop(te, d, 10, (i // len(sets)) % 10, n_surr=int(rng.integers(100, 1001)),
+                          seed=7, tag_base=tag0 + (i << 20), loop_id=i)
+
+    te.te_serve_start(ctx, hbm_budget_bytes=16 << 30, max_inflight=2, max_batch_jobs=512)
+    warm = [make(i, 1 << 41) for i in range(len(sets))]
+    for lp in warm:   # one request of every data set
+        req = lp.next_request()
+        tk = [te.te_serve_submit(ctx, j) for j in req.jobs]
+        for t, j in zip(tk, req.jobs):
+            te.te_serve_poll(ctx, t, j.n_surr)
+    loops = [make(i, 1 << 42) for i in range(n_loops)]
+    t0 = time.perf_counter()
+    reqs = run_served(te, ctx, loops, deadline_s=seconds)
+    span = max(r.t_done for r in reqs) - t0
+    st = te.te_serve_get_stats(ctx)
+    te.te_serve_stop(ctx)
+    lat = np.array([(r.t_done - r.t_submit) * 1e3 for r in reqs])
+    est = sum(r.estimates for r in reqs)
+    jobs = [j for r in reqs for j in r.jobs]
+    pick = [jobs[int(a)] for a in rng.integers(0, len(jobs), plain_calls)]
+    te.cmi_ksg(ctx, pick[0].data, pick[0].x, pick[0].y, pick[0].z, k=4, max_lag=5)
+    t1 = time.perf_counter()
+    for j in pick:
+        te.cmi_ksg(ctx, j.data, j.x, j.y, j.z, k=4, max_lag=5)
+    plain = plain_calls / (time.perf_counter() - t1)
+    served = est / span
+    by_stage = {}
+    for r in reqs:
+        by_stage[r.stage] = by_stage.get(r.stage, 0) + 1
+    ctx.close()
+    return {"value": served, "unit": UNIT, "loops": n_loops, "seconds": round(span, 2),
+            "requests": len(reqs), "requests_by_stage": by_stage, "estimates": est,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "plain_estimates_per_s": plain, "served_over_plain": served / plain,
+            "loops_finished": sum(1 for lp in loops if lp.done), "batches": st["batches"],
+            "peak_admitted_bytes": st["peak_bytes"],
+            "workload": "100 greedy target loops (steps 1-4 of one target each) over 6 data "
+                        "sets of 10 processes: CLM and VAR at T = 1000, 3000, 10000; "
+                        "S ~ U{100..1000} per loop; every test one request of one job per "
+                        "candidate; max_inflight 2, 16 GiB admission budget"}
 
 
 def run_gauss(args):
@@ -452,6 +518,8 @@ def main():
     ap.add_argument("--serve", action="store_true",
                     help="run the serving workload instead of the network benchmark")
     ap.add_argument("--serve-requests", type=int, default=80)
+    ap.add_argument("--serve-seconds", type=float, default=15.0,
+                    help="length of the greedy-loop serving phase (extra key 'serving')")
     ap.add_argument("--gauss", action="store_true",
                     help="linear-Gaussian estimator path (cmi_gauss) instead of the KSG network")
     ap.add_argument("--gauss-network", action="store_true",
@@ -635,6 +703,8 @@ def main():
         line["plain_path"]["batched_over_plain"] = value / line["plain_path"]["value"]
     if args.extra and args.workload != "var10" and world == 1:
         line["var10_network"] = var10_network(te, ctx, stream, args.T)
+    if args.extra and world == 1:
+        line["serving"] = serve_greedy(te, seconds=args.serve_seconds)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_oracle_sample(series, params)
         one = cpu_oracle_sample(series, params, members=3, threads=1)

@@ -97,3 +97,65 @@ def test_cancel_budget_and_timeout(env):
     with pytest.raises(te.TEError, match="TE_EINVAL"):
         te.te_serve_poll(ctx, t1, 400)         # released
     te.te_serve_stop(ctx)
+
+
+def test_greedy_loops_served_equal_direct_and_oracle():
+    """Six greedy target loops (steps 1-4 of one target each, every test one
+    request of one job per candidate) run concurrently against one server;
+    each loop takes exactly the requests and decisions of the same loop whose
+    tests run directly through cmi_ksg_batch, every key equal, and sampled
+    served jobs equal the CPU oracle's keys (permutations drawn from the
+    jobs' seed and stream tag)."""
+    import paper_1902_06828_gb300 as te
+    from oracle import ksg as oksg
+    from paper_1902_06828_gb300.serve_loops import TargetLoop, run_served
+    ctx = te.Context(0)
+    sets = []
+    for kind, T, seed in (("clm", 500, 3), ("var", 700, 4)):
+        x = (synth.clm_er(n=4, T=T, seed=seed, max_lag=3)[0] if kind == "clm"
+             else synth.var_er(n=4, p=0.5, T=T, seed=seed, lo=0.4, hi=0.7, max_lag=3)[0])
+        s = synth.standardise_jitter(x, seed)
+        sets.append((te.te_data_create(ctx, s), s))
+
+    def loops():
+        return [TargetLoop(te, sets[i % 2][0], 4, i // 2, n_surr=30 + 10 * i, alpha=0.1,
+                           max_lag=3, seed=5, tag_base=1000 * (i + 1), loop_id=i)
+                for i in range(6)]
+
+    lk = threading.Lock()   # a context serves one thread at a time
+
+    def direct_eval(r):
+        with lk:
+            return te.cmi_ksg_batch(ctx, r.jobs, return_keys=True)[1]
+
+    direct_loops = loops()
+    direct = run_served(te, ctx, direct_loops, evaluate=direct_eval)
+    te.te_serve_start(ctx, hbm_budget_bytes=1 << 30, max_inflight=2, max_batch_jobs=64)
+    try:
+        served_loops = loops()
+        served = run_served(te, ctx, served_loops)
+    finally:
+        te.te_serve_stop(ctx)
+    assert all(lp.done for lp in served_loops)
+    key = lambda r: (r.loop, r.stage, r.it)
+    d_by = {key(r): r for r in direct}
+    assert sorted(d_by) == sorted(key(r) for r in served)
+    for r in served:
+        assert r.keys == d_by[key(r)].keys, key(r)
+    for a, b in zip(served_loops, direct_loops):
+        assert a.result() == b.result()
+    assert any(r.stage == 2 for r in served) and any(lp.sel_x for lp in served_loops)
+    # the oracle on a sample of served jobs
+    rng = np.random.default_rng(2)
+    jobs = [(j, r.keys[a]) for r in served for a, j in enumerate(r.jobs)]
+    for i in rng.choice(len(jobs), 8, replace=False):
+        j, got = jobs[int(i)]
+        s = sets[0][1] if j.data is sets[0][0] else sets[1][1]
+        N = s.shape[1] - j.max_lag
+        perms = np.stack([oksg.permutation(j.seed, j.stream_tag, 0, 0, q, N)
+                          for q in range(1, j.n_surr + 1)])
+        want, _, _ = oksg.cmi_ksg_batch(s, [j.x] * (j.n_surr + 1), j.y, j.z, perms=perms,
+                                        perm_idx=[-1] + list(range(j.n_surr)), k=j.k,
+                                        max_lag=j.max_lag)
+        assert got == want
+    ctx.close()
