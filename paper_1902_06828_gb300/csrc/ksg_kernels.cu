@@ -691,13 +691,18 @@ __device__ __forceinline__ void ksg_lane_item(const KsgLaunch &L, const CUtensor
     auto yz_off = [&](int d) {
         return d < dy ? L.cols[G.ycol + d] : L.cols[G.zcol + d - dy];
     };
-    const int qbase = qtile * LQC + warp * LQ;   // first query position of this warp
+    // The warp's LQ query points are positions qbase + LW a of the CTA's LQC
+    // consecutive ones (interleaved, not adjacent): neighbouring points have
+    // similar neighbourhoods, so interleaving evens out the warps' work per
+    // tile, which the per-tile barrier otherwise pays at the slowest warp.
+    const int qbase = qtile * LQC + warp;
+    auto qpos = [&](int a) { return qbase + LW * a; };
 
     // ---- the warp's query points ----
     float xi[LQ][MS];
 #pragma unroll
     for (int a = 0; a < LQ; ++a) {
-        const int qc = min(qbase + a, N - 1);
+        const int qc = min(qpos(a), N - 1);
 #pragma unroll
         for (int q = 0; q < MS; ++q) {
             if constexpr (TMA) {
@@ -711,7 +716,7 @@ __device__ __forceinline__ void ksg_lane_item(const KsgLaunch &L, const CUtensor
     }
     for (int e = lane; e < LQ * dyz; e += 32) {
         const int a = e / dyz, d = e - a * dyz;
-        const int qc = min(qbase + a, N - 1);
+        const int qc = min(qpos(a), N - 1);
         s_q[(warp * LQ + a) * dyz + d] = sorted ? G.yz[(size_t)d * N + qc] : base[yz_off(d) + qc];
     }
     if (lane < LQ) s_bound[warp][lane] = CUDART_INF_F;
@@ -924,7 +929,7 @@ __device__ __forceinline__ void ksg_lane_item(const KsgLaunch &L, const CUtensor
                     dyzv = fmaxf(dyzv, fabsf(__fsub_rn(qc[d], tp[d * jt])));
             }
             const int j = j0 + c + u;
-            const int qp = min(qbase + a, N - 1);
+            const int qp = min(qpos(a), N - 1);
             const int gap = j > qp ? j - qp : qp - j;
             if (j >= N || gap <= w) {
                 dzv = CUDART_INF_F;
@@ -1156,10 +1161,10 @@ __device__ __forceinline__ void ksg_lane_item(const KsgLaunch &L, const CUtensor
 #pragma unroll
         for (int a = 0; a < LQ; ++a) {
             const int nz = (int)cz[a][q], nxz = (int)cxz[a][q], nyz = (int)cyz[a][q];
-            if (qbase + a < N) {
+            if (qpos(a) < N) {
                 term += L.q[nz + 1] - L.q[nxz + 1] - L.q[nyz + 1];
                 if (L.dbg_eps && mvalid[q] && md[q].out == L.dbg_out) {
-                    const int tq = sorted ? G.sigma[qbase + a] : qbase + a;
+                    const int tq = sorted ? G.sigma[qpos(a)] : qpos(a);
                     L.dbg_eps[tq] = eps[a][q];
                     L.dbg_nxz[tq] = nxz;
                     L.dbg_nyz[tq] = nyz;
