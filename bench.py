@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "KSG CMI estimates/s incl. surrogates at T=10000"
 UNIT = "estimates/s"
-TRAFFIC_PER_MEMBER_POINT = (146434560.0 + 4099584.0) / (9045 * 3995)
+TRAFFIC_PER_MEMBER_POINT = (147021056.0 + 4220672.0) / (9045 * 3995)
 
 
 def _peaks():
@@ -589,12 +589,17 @@ def main():
     barrier()
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    step_est = []
     ev0.record(stream)
-    for _ in range(args.steps):
+    step_ev[0].record(stream)
+    for a in range(args.steps):
         if flush is not None:
             flush.fill_(1)
         r = step(data)
         n_est += r["n_estimates"]
+        step_est.append(r["n_estimates"])
+        step_ev[a + 1].record(stream)
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
@@ -605,8 +610,13 @@ def main():
         desc += (f"; one step = the complete greedy inference of one target; warm-up targets "
                  f"0-{first_timed - 1}, timed targets {first_timed}-{last} (mod {n_proc})")
 
-    # end to end through the C ABI with host buffers
-    e2e_steps = args.e2e_steps if args.e2e_steps is not None else min(args.steps, 3)
+    # end to end through the C ABI with host buffers, over the same work as
+    # the first e2e_steps timed steps (per target: the same targets again)
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else min(args.steps, 5)
+    e2e_steps = min(e2e_steps, args.steps)
+    counter[0] = first_timed
+    same_ms = sum(step_ev[a].elapsed_time(step_ev[a + 1]) for a in range(e2e_steps))
+    same_est = sum(step_est[:e2e_steps])
     host = torch.from_numpy(series).pin_memory()
     e_est = 0
     sb = ctx.stats()
@@ -643,10 +653,11 @@ def main():
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     peak = sm_count * 128 * sm_max * 1e6 / 1e12
     # DRAM traffic of the KSG kernel per launch: the ncu capture of the same
-    # kernel (T = 4000, step-2 launch of target 0, 9045 members x 3995 points)
-    # read 146.43 MB and wrote 4.10 MB, i.e. 4.17 bytes per member-point (each
-    # member's X row read once); scaled here by the member-points one launch
-    # processes.  Algorithmic bytes: 4 N per member (its X row) + 16 (key).
+    # kernel (var10 at T = 4000, step-2 launch of target 0, 9045 members x 3995
+    # points) read 147.02 MB and wrote 4.22 MB, i.e. 4.19 bytes per
+    # member-point (each member's X row read once); scaled here by the
+    # member-points one launch processes.  Algorithmic bytes: 4 N per member
+    # (its X row) + 16 (key).
     n_pts = args.T - 5
     mp_per_launch = (n_est / world) * n_pts / max(ksg_launches, 1)   # this rank's launches
     traffic = TRAFFIC_PER_MEMBER_POINT * mp_per_launch if ksg_launches else None
@@ -672,7 +683,11 @@ def main():
         "e2e": {"value": e_est / (e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": (se["h2d_bytes"] - sb["h2d_bytes"]) / max(e2e_steps, 1),
                 "d2h_bytes_per_step": (se["d2h_bytes"] - sb["d2h_bytes"]) / max(e2e_steps, 1),
-                "steps": e2e_steps},
+                "steps": e2e_steps,
+                "device_resident_same_steps": (same_est / (same_ms / 1e3)) if same_ms > 0
+                else None,
+                "note": "the work of the first timed steps again (same targets), each step "
+                        "uploading the series from pinned host memory"},
         "gpu_launches": s1["launches"] - s0["launches"],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
