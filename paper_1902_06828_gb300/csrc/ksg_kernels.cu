@@ -762,6 +762,15 @@ __device__ __forceinline__ void ksg_lane_item(const KsgLaunch &L, const CUtensor
         return __ballot_sync(0xffffffffu, any != 0);
     };
 
+    // this warp's live chunks of the tile (any of its query points), a subset
+    // of the CTA mask: the chunk loop visits only these
+    auto warp_mask = [&](int jn) {
+        const int nct = (jn + 7) >> 3;
+        unsigned any = 0;
+        if (lane < nct) any = (s_bits[warp * wpt + (lane >> 3)] >> (4 * (lane & 7))) & 0xFu;
+        return __ballot_sync(0xffffffffu, any != 0);
+    };
+
     // stage the live chunks: thread = (member m, point u) for X, (dim, point)
     // for Y and Z; four chunks per round keep several gathers in flight
     auto stage = [&](int j0, unsigned mask) {
@@ -910,6 +919,9 @@ __device__ __forceinline__ void ksg_lane_item(const KsgLaunch &L, const CUtensor
     // in the pass's shared subspace (d_YZ in pass 1, d_Z in pass 2); with the
     // bound >= every member's threshold or eps, no member can insert or count
     // one of them.
+    // this lane's (query, point) of the distance step: query a = lane / 8 at
+    // position qp_lane (clamped to the data), point u = lane % 8 of the chunk
+    const int qp_lane = min(qpos(lane >> 3), N - 1);
     auto chunk_dist = [&](int j0, int c, unsigned live4, bool pass1) {
         const int a = lane >> 3, u = lane & 7;
         float dzv = -CUDART_INF_F, dyzv = -CUDART_INF_F;
@@ -929,8 +941,7 @@ __device__ __forceinline__ void ksg_lane_item(const KsgLaunch &L, const CUtensor
                     dyzv = fmaxf(dyzv, fabsf(__fsub_rn(qc[d], tp[d * jt])));
             }
             const int j = j0 + c + u;
-            const int qp = min(qpos(a), N - 1);
-            const int gap = j > qp ? j - qp : qp - j;
+            const int gap = abs(j - qp_lane);
             if (j >= N || gap <= w) {
                 dzv = CUDART_INF_F;
                 dyzv = CUDART_INF_F;
@@ -991,7 +1002,7 @@ __device__ __forceinline__ void ksg_lane_item(const KsgLaunch &L, const CUtensor
             if (!any) continue;
             const unsigned mask = cta_mask(jn);
             if (!stage_all(j0, jn, mask)) return;
-            unsigned rest = mask;
+            unsigned rest = mask & warp_mask(jn);
             while (rest) {
                 const int c = (__ffs(rest) - 1) * JC;
                 rest &= rest - 1;
@@ -1115,7 +1126,7 @@ __device__ __forceinline__ void ksg_lane_item(const KsgLaunch &L, const CUtensor
         if (!any) continue;
         const unsigned mask = cta_mask(jn);
         if (!stage_all(j0, jn, mask)) return;
-        unsigned rest = mask;
+        unsigned rest = mask & warp_mask(jn);
         while (rest) {
             const int c = (__ffs(rest) - 1) * JC;
             rest &= rest - 1;
