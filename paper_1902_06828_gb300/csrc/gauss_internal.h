@@ -70,12 +70,13 @@ __host__ __device__ inline double gauss_f64_gamma(int N)
     return nu / (1.0 - nu);
 }
 // estimates with dw <= kGaussFFMaxW take the float-float contraction instead:
-// 3 * 2^-48 per product and at most 32^2 * 2^-48 per 32-point window (2^-37
-// covers both), then the FP64 sums
+// 3 * 2^-48 per product and at most 128^2 * 2^-48 per window of kGaussFFWindow
+// 32-point chunks (2^-34 covers both), then the FP64 sums
 constexpr int kGaussFFMaxW = 16;
+constexpr int kGaussFFWindow = 4;
 __host__ __device__ inline double gauss_batch_gamma(int N, int dw)
 {
-    return gauss_f64_gamma(N) + (dw <= kGaussFFMaxW ? 0x1p-37 : 0.0);
+    return gauss_f64_gamma(N) + (dw <= kGaussFFMaxW ? 0x1p-34 : 0.0);
 }
 // the whole FP64 pipeline (means, covariance, factors, centred X columns into
 // xc, FP64 contraction and its reduction, Schur complements) for n <= 65535

@@ -651,6 +651,11 @@ __device__ __forceinline__ void gauss_cross_ff_body(const GaussArgs &A, int bx, 
     const int nchunks = (A.N + kGaussKC - 1) / kGaussKC;
     const int c0 = by * A.chunks_per_split;
     const int c1 = min(nchunks, c0 + A.chunks_per_split);
+    // the float pair sums kGaussFFWindow chunks (128 points) before each FP64
+    // flush: the flushes run on GB300's narrow FP64 pipe
+    float sh[DW], sl[DW];
+#pragma unroll
+    for (int w = 0; w < DW; ++w) sh[w] = sl[w] = 0.f;
     for (int c = c0; c < c1; ++c) {
         const int t0 = c * kGaussKC, n = min(kGaussKC, A.N - t0);
         __syncthreads();
@@ -666,9 +671,6 @@ __device__ __forceinline__ void gauss_cross_ff_body(const GaussArgs &A, int bx, 
         }
         __syncthreads();
         if (!live) continue;
-        float sh[DW], sl[DW];
-#pragma unroll
-        for (int w = 0; w < DW; ++w) sh[w] = sl[w] = 0.f;
         for (int t8 = 0; t8 < n; t8 += 8) {
             // eight permutation entries, then eight X values, before any is used
             int src[8];
@@ -700,8 +702,13 @@ __device__ __forceinline__ void gauss_cross_ff_body(const GaussArgs &A, int bx, 
                 }
             }
         }
+        if ((c - c0) % kGaussFFWindow == kGaussFFWindow - 1 || c == c1 - 1) {
 #pragma unroll
-        for (int w = 0; w < DW; ++w) acc[w] += (double)sh[w] + (double)sl[w];
+            for (int w = 0; w < DW; ++w) {
+                acc[w] += (double)sh[w] + (double)sl[w];
+                sh[w] = sl[w] = 0.f;
+            }
+        }
     }
     if (!live) return;
     double *dst = A.cross_part + ((size_t)by * rows + row) * dw;
