@@ -25,7 +25,7 @@ import synth
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-CASES = [("var10", 0)]
+CASES = [("var10", 0), ("clm100", 5)]
 
 
 def _keys_sha(keys):
