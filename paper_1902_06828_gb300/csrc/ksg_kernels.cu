@@ -1002,9 +1002,15 @@ __device__ __forceinline__ void ksg_lane_item(const KsgLaunch &L, const CUtensor
             if (!any) continue;
             const unsigned mask = cta_mask(jn);
             if (!stage_all(j0, jn, mask)) return;
+            // The home tile starts with every threshold at +inf: its chunks are
+            // visited from the CTA's own positions on (nearest first), so that
+            // the thresholds fall early and fewer points are inserted.
+            const bool home_tile = s == 0 && sorted;
+            const int rot = home_tile ? (((qtile * LQC) - j0) >> 3) & 31 : 0;
             unsigned rest = mask & warp_mask(jn);
+            if (rot) rest = (rest >> rot) | (rest << (32 - rot));
             while (rest) {
-                const int c = (__ffs(rest) - 1) * JC;
+                const int c = ((__ffs(rest) - 1 + rot) & 31) * JC;
                 rest &= rest - 1;
                 const unsigned live4 = (s_bits[warp * wpt + (c >> 6)] >> (4 * ((c >> 3) & 7))) & 0xFu;
                 if (!live4) continue;
