@@ -53,6 +53,45 @@ __device__ __forceinline__ float topk_at(const float (&b)[K], int idx)
     return r;
 }
 
+// Compare-exchange: (a, b) <- (min, max).
+__device__ __forceinline__ void cmpx(float &a, float &b)
+{
+    const float lo = fminf(a, b);
+    b = fmaxf(a, b);
+    a = lo;
+}
+
+// b (ascending, 4 values) <- the 4 smallest of b and the 8 values D, ascending,
+// with multiplicity: each half of D is sorted by a 5-comparator network, and
+// each sorted half is merged into b by taking min(b[i], h[3 - i]) (the 4
+// smallest of the two lists, a bitonic sequence) and sorting that by a
+// 4-comparator bitonic network.  Comparator networks permute their inputs, so
+// the result is exactly the multiset's 4 smallest; when no D is below b[3] it
+// returns b unchanged.  Branch-free: 44 min/max operations.
+__device__ __forceinline__ void top4_merge8(float (&b)[4], const float (&D)[JC])
+{
+    float h[2][4];
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) h[g][i] = D[4 * g + i];
+        cmpx(h[g][0], h[g][1]);
+        cmpx(h[g][2], h[g][3]);
+        cmpx(h[g][0], h[g][2]);
+        cmpx(h[g][1], h[g][3]);
+        cmpx(h[g][1], h[g][2]);
+    }
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) b[i] = fminf(b[i], h[g][3 - i]);
+        cmpx(b[0], b[2]);
+        cmpx(b[1], b[3]);
+        cmpx(b[0], b[1]);
+        cmpx(b[2], b[3]);
+    }
+}
+
 __device__ __forceinline__ void load8(const float *p, float (&v)[JC])
 {
     const float4 a = *reinterpret_cast<const float4 *>(p);
@@ -1034,7 +1073,16 @@ __device__ __forceinline__ void ksg_lane_item(const KsgLaunch &L, const CUtensor
                         // one test for the 8 points; the insertions are the rare path
                         const float mn = fminf(fminf(fminf(D[0], D[1]), fminf(D[2], D[3])),
                                                fminf(fminf(D[4], D[5]), fminf(D[6], D[7])));
-                        if (mn < thr[a][q]) {
+                        if constexpr (KT == 4) {
+                            // Some lane of the warp has a point below its threshold
+                            // on about 70% of the chunks (32 members per warp), so
+                            // the whole chunk is merged without branches by every
+                            // lane (a no-op for lanes without one).
+                            if (__any_sync(0xffffffffu, mn < thr[a][q])) {
+                                top4_merge8(buf[a][q], D);
+                                thr[a][q] = buf[a][q][3];
+                            }
+                        } else if (mn < thr[a][q]) {
 #pragma unroll
                             for (int u = 0; u < JC; ++u) {
                                 if (D[u] < thr[a][q]) {
@@ -1503,86 +1551,190 @@ __global__ void fisher_yates_kernel(int32_t *out, long long stride, int n, uint6
             out[(long long)blockIdx.x * stride + i] = sperm[i];
 }
 
-// ---------------- spatial order: Morton curve over (Y, Z) ----------------
-// One CTA per group: per-dimension ranges, Morton keys (bits interleaved
-// from the most significant, up to 50 bits) packed with the point index, a
-// bitonic sort in shared memory, then the sorted coordinates and the bounding
-// box of every aligned chunk of 8 sorted points.  The order only affects how
-// much work the pruning saves, never a result.
+// ---------------- spatial order: k-d tree over (Y, Z) ----------------
+// The points of a group are put in the leaf order of a k-d tree over the
+// (Y, Z) space.  A node of m > 8 points is split at the median of its widest
+// dimension into a first child of `kd_left(m)` points and a second child of
+// the rest; the first child's size is a multiple of 256 (nodes above 256
+// points) or of 8, so every node starts on a multiple of 8 (of 256 above 256
+// points), and every aligned 8-point chunk and 256-point tile is a union of
+// whole nodes: their bounding boxes, which the pruning tests, stay compact in
+// every dimension.  The order only affects how much work the pruning saves,
+// never a result.
+constexpr int kOrderMaxSeg = 2048;   // nodes that still split at one level (> 8 points: N / 9)
+constexpr size_t kOrderSmem = (size_t)kMaxOrderN * 8 + (size_t)kMaxOrderN * 2 +
+                              6 * (size_t)kOrderMaxSeg * 4;
+
+// float <-> uint32 with the same order (finite values and infinities)
+__device__ __forceinline__ unsigned ordered_u32(float v)
+{
+    const unsigned b = __float_as_uint(v);
+    return b ^ ((b >> 31) ? 0xFFFFFFFFu : 0x80000000u);
+}
+__device__ __forceinline__ float ordered_f32(unsigned u)
+{
+    return __uint_as_float(u ^ ((u >> 31) ? 0x80000000u : 0xFFFFFFFFu));
+}
+
+// points of the first child of a node of m > 8 points: the multiple of 256
+// (m > 256) or of 8 nearest to m / 2, at least one block and below m
+__device__ __forceinline__ int kd_left(int m)
+{
+    const int blk = m > 256 ? 256 : 8;
+    const int left = (m + blk) / (2 * blk) * blk;
+    return left < blk ? blk : (left > m - 1 ? m - 1 : left);
+}
+
+// One CTA per group.  The tree is built level by level over the current
+// order: every node that still splits (the active nodes, start-ordered) finds
+// its widest dimension from per-dimension extents (segmented warp scans over
+// consecutive positions, then shared-memory atomics), and one bitonic sort of
+// the keys (node start, coordinate on that dimension, point) orders every
+// active node along its dimension at once; points of finished leaves key on
+// their own position and stay.  Then the sorted coordinates and the bounding
+// box of every aligned chunk of 8 and tile of 256 sorted points.
 __global__ void __launch_bounds__(1024) order_kernel(const OrderJob *jobs)
 {
-    extern __shared__ unsigned long long skeys[];
-    __shared__ float s_lo[32], s_hi[32];
-    __shared__ float s_red[2][32];
+    extern __shared__ unsigned long long skeys[];                 // [P2]
+    short *s_seg = reinterpret_cast<short *>(skeys + kMaxOrderN); // [N] active node of a position, -1 none
+    int *s_start = reinterpret_cast<int *>(s_seg + kMaxOrderN);   // [kOrderMaxSeg] active nodes
+    int *s_size = s_start + kOrderMaxSeg;
+    unsigned *s_lo = reinterpret_cast<unsigned *>(s_size + kOrderMaxSeg);
+    unsigned *s_hi = s_lo + kOrderMaxSeg;
+    float *s_ext = reinterpret_cast<float *>(s_hi + kOrderMaxSeg);
+    int *s_dim = reinterpret_cast<int *>(s_ext + kOrderMaxSeg);
+    __shared__ int s_nact;
     const OrderJob &J = jobs[blockIdx.x];
     const int N = J.N, D = J.dyz;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int nw = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const float *base = J.base;
-    for (int d = 0; d < D; ++d) {
-        float mn = CUDART_INF_F, mx = -CUDART_INF_F;
-        for (int p = tid; p < N; p += blockDim.x) {
-            const float v = base[J.cols[d] + p];
-            mn = fminf(mn, v);
-            mx = fmaxf(mx, v);
-        }
-        mn = warp_min(mn);
-        mx = warp_max(mx);
-        if (lane == 0) {
-            s_red[0][wid] = mn;
-            s_red[1][wid] = mx;
-        }
-        __syncthreads();
-        if (wid == 0) {
-            mn = lane < nw ? s_red[0][lane] : CUDART_INF_F;
-            mx = lane < nw ? s_red[1][lane] : -CUDART_INF_F;
-            mn = warp_min(mn);
-            mx = warp_max(mx);
-            if (lane == 0) {
-                s_lo[d] = mn;
-                s_hi[d] = mx;
-            }
-        }
-        __syncthreads();
-    }
-    int bits = 50 / D;
-    if (bits > 24) bits = 24;
-    if (bits < 1) bits = 1;
-    const float qmax = (float)((1u << bits) - 1u);
     int P2 = 1;
     while (P2 < N) P2 <<= 1;
-    for (int p = tid; p < P2; p += blockDim.x) {
-        unsigned long long key = ~0ull;
-        if (p < N) {
-            unsigned long long mort = 0;
-            unsigned int q[32];
-            for (int d = 0; d < D; ++d) {
-                const float span = s_hi[d] - s_lo[d];
-                float f = span > 0.f ? (base[J.cols[d] + p] - s_lo[d]) / span * qmax : 0.f;
-                f = fminf(fmaxf(f, 0.f), qmax);
-                q[d] = (unsigned int)f;
-            }
-            for (int b = bits - 1; b >= 0; --b)
-                for (int d = 0; d < D; ++d) mort = (mort << 1) | ((q[d] >> b) & 1u);
-            key = (mort << 14) | (unsigned long long)p;
-        }
-        skeys[p] = key;
+    for (int p = tid; p < P2; p += blockDim.x) skeys[p] = p < N ? (unsigned long long)p : ~0ull;
+    if (tid == 0) {
+        s_start[0] = 0;
+        s_size[0] = N;
+        s_nact = N > 8 ? 1 : 0;
     }
     __syncthreads();
-    for (int kk = 2; kk <= P2; kk <<= 1) {
-        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-            for (int t = tid; t < (P2 >> 1); t += blockDim.x) {
-                const int lo = 2 * jj * (t / jj) + (t % jj);
-                const int hi = lo + jj;
-                const bool up = (lo & kk) == 0;
-                const unsigned long long x = skeys[lo], y = skeys[hi];
-                if ((x > y) == up) {
-                    skeys[lo] = y;
-                    skeys[hi] = x;
+    while (s_nact > 0) {
+        const int nact = s_nact;
+        // the active node of every position (last one starting at or before it)
+        for (int p = tid; p < N; p += blockDim.x) {
+            int lo = 0, hi = nact - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_start[mid] <= p) lo = mid;
+                else hi = mid - 1;
+            }
+            s_seg[p] = (s_start[lo] <= p && p < s_start[lo] + s_size[lo]) ? (short)lo : (short)-1;
+        }
+        for (int s = tid; s < nact; s += blockDim.x) {
+            s_ext[s] = -1.f;
+            s_dim[s] = 0;
+        }
+        __syncthreads();
+        // widest dimension of every active node (first one on ties)
+        for (int d = 0; d < D; ++d) {
+            for (int s = tid; s < nact; s += blockDim.x) {
+                s_lo[s] = 0xFFFFFFFFu;
+                s_hi[s] = 0u;
+            }
+            __syncthreads();
+            for (int p0 = 0; p0 < N; p0 += blockDim.x) {   // whole warps: the scan shuffles
+                const int p = p0 + tid;
+                int sg = -1;
+                unsigned v = 0u;
+                if (p < N) {
+                    sg = s_seg[p];
+                    if (sg >= 0) v = ordered_u32(base[J.cols[d] + (int)(skeys[p] & 0x3FFFull)]);
+                }
+                unsigned mn = v, mx = v;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const unsigned a = __shfl_up_sync(0xffffffffu, mn, off);
+                    const unsigned b = __shfl_up_sync(0xffffffffu, mx, off);
+                    const int so = __shfl_up_sync(0xffffffffu, sg, off);
+                    if (lane >= off && so == sg) {   // nodes are contiguous runs of positions
+                        mn = min(mn, a);
+                        mx = max(mx, b);
+                    }
+                }
+                const int sn = __shfl_down_sync(0xffffffffu, sg, 1);
+                if (sg >= 0 && (lane == 31 || sn != sg)) {
+                    atomicMin(&s_lo[sg], mn);
+                    atomicMax(&s_hi[sg], mx);
+                }
+            }
+            __syncthreads();
+            for (int s = tid; s < nact; s += blockDim.x) {
+                const float e = ordered_f32(s_hi[s]) - ordered_f32(s_lo[s]);
+                if (e > s_ext[s]) {
+                    s_ext[s] = e;
+                    s_dim[s] = d;
                 }
             }
             __syncthreads();
         }
+        // keys: (node start, coordinate on its dimension, point) for active
+        // positions, (own position, point) for the others
+        for (int p = tid; p < N; p += blockDim.x) {
+            const unsigned long long idx = skeys[p] & 0x3FFFull;
+            const int sg = s_seg[p];
+            unsigned long long key = ((unsigned long long)p << 46) | idx;
+            if (sg >= 0) {
+                const float v = base[J.cols[s_dim[sg]] + (int)idx];
+                key = ((unsigned long long)s_start[sg] << 46) |
+                      ((unsigned long long)ordered_u32(v) << 14) | idx;
+            }
+            skeys[p] = key;
+        }
+        __syncthreads();
+        for (int kk = 2; kk <= P2; kk <<= 1) {
+            for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                for (int t = tid; t < (P2 >> 1); t += blockDim.x) {
+                    const int lo = 2 * jj * (t / jj) + (t % jj);
+                    const int hi = lo + jj;
+                    const bool up = (lo & kk) == 0;
+                    const unsigned long long x = skeys[lo], y = skeys[hi];
+                    if ((x > y) == up) {
+                        skeys[lo] = y;
+                        skeys[hi] = x;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int p = tid; p < N; p += blockDim.x) skeys[p] &= 0x3FFFull;
+        // the children that still split, in order (one warp; written to the
+        // extent arrays, free now, then copied back)
+        if (tid < 32) {
+            int out = 0;
+            for (int c0 = 0; c0 < 2 * nact; c0 += 32) {
+                const int c = c0 + lane;
+                int st = 0, sz = 0;
+                if (c < 2 * nact) {
+                    const int s = c >> 1, m = s_size[s], left = kd_left(m);
+                    st = s_start[s] + ((c & 1) ? left : 0);
+                    sz = (c & 1) ? m - left : left;
+                }
+                const bool act = sz > 8;
+                const unsigned bal = __ballot_sync(0xffffffffu, act);
+                if (act) {
+                    const int o = out + __popc(bal & ((1u << lane) - 1u));
+                    s_lo[o] = (unsigned)st;
+                    s_hi[o] = (unsigned)sz;
+                }
+                out += __popc(bal);
+            }
+            __syncwarp();
+            for (int s = lane; s < out; s += 32) {
+                s_start[s] = (int)s_lo[s];
+                s_size[s] = (int)s_hi[s];
+            }
+            if (lane == 0) s_nact = out;
+        }
+        __syncthreads();
     }
     for (int p = tid; p < N; p += blockDim.x) {
         const int t = (int)(skeys[p] & 0x3FFFull);
@@ -1826,7 +1978,7 @@ cudaError_t ksg_prepare_attributes()
         }
     cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(&order_kernel),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kMaxOrderN * 8);
+                                         (int)kOrderSmem);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(reinterpret_cast<const void *>(&stats_kernel),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -1863,7 +2015,7 @@ cudaError_t launch_compose(const ComposeJob *jobs, int n_jobs, int max_n, cudaSt
 cudaError_t launch_order(const OrderJob *jobs, int n_jobs, cudaStream_t st)
 {
     if (n_jobs <= 0) return cudaSuccess;
-    order_kernel<<<n_jobs, 1024, kMaxOrderN * 8, st>>>(jobs);
+    order_kernel<<<n_jobs, 1024, kOrderSmem, st>>>(jobs);
     return cudaGetLastError();
 }
 
