@@ -24,7 +24,7 @@ struct GroupDesc {
     int n_mblocks;          // ceil(n_members / members per thread)
     long long item_begin;   // first CTA of the group in the launch
     // Spatial order (nullptr sigma = time order).  Points are processed in the
-    // order of a Morton curve over the shared (Y, Z) coordinates: position p is
+    // leaf order of a k-d tree over the shared (Y, Z) coordinates: position p is
     // time point sigma[p]; yz[d * N + p] holds Y (d < dy) and Z coordinates in
     // that order; box[d * n_chunks8 + c] = (min, max) of dim d over positions
     // 8c .. 8c + 7.  Only used with theiler == 0.
@@ -39,8 +39,9 @@ struct GroupDesc {
     const float *ysorted;
 };
 
-// One spatial-order job (one CTA): Morton keys of the (Y, Z) coordinates of a
-// group, sorted in shared memory; writes sigma, yz and box as described above.
+// One spatial-order job (one CTA): the k-d tree order of the (Y, Z) coordinates
+// of a group, built in shared memory; writes sigma, yz, box and tbox as
+// described above.
 struct OrderJob {
     const float *base;
     int N, dyz;

@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(QT) ksg_fused_kernel(const KsgLaunch L)
     const int jt = L.jt;
     const int cpt = jt >> 3;                  // chunks of 8 per tile
     const float *__restrict__ base = G.base;
-    const bool sorted = G.sigma != nullptr;   // Morton order over (Y, Z), theiler == 0
+    const bool sorted = G.sigma != nullptr;   // k-d tree order over (Y, Z), theiler == 0
 
     const int rows_t = dyz + M * dx;
     const int rows_q = dyz + (DX1 ? 0 : M * dx);
