@@ -692,6 +692,10 @@ __device__ __forceinline__ void ksg_lane_item(const KsgLaunch &L, const CUtensor
     __shared__ float s_bound[LW][LQ];
     __shared__ long long s_red[LW][MB];
     __shared__ float2 s_cqbox[32];
+    // per pass, the lower bound from the CTA's query box to every tile box
+    // (pass 1 over (Y, Z), pass 2 over Z): tile t is skipped when it reaches
+    // the CTA's largest bound
+    __shared__ float s_tlb[2][kMaxOrderN / 256];
     __shared__ __align__(8) unsigned long long s_tbar;   // tile-copy mbarrier (TMA)
     const uint32_t tbar = lane_smem_u32(&s_tbar);
     uint32_t tphase = 0;
@@ -760,31 +764,38 @@ __device__ __forceinline__ void ksg_lane_item(const KsgLaunch &L, const CUtensor
     }
     if (lane < LQ) s_bound[warp][lane] = CUDART_INF_F;
     __syncthreads();
-    // bounding box of the CTA's 32 query points, for the coarse tile test
-    if (sorted && warp == 0) {
+    // Coarse test, taken identically by every thread without a barrier: it
+    // reads the tile bounds (written before the barrier below) and `bound`, a
+    // register snapshot of the CTA's largest per-query bound taken right
+    // after a barrier.
+    const bool coarse = sorted && jt == 256 && G.tbox != nullptr;
+    // bounding box of the CTA's 32 query points, then its lower bound to every
+    // tile box for both passes (one warp; N <= kMaxOrderN on this path)
+    if (coarse && warp == 0) {
         for (int d = 0; d < dyz; ++d) {
             const float v = s_q[lane * dyz + d];   // query lane of the CTA (warp lane/4, a lane%4)
             const float mn = warp_min(v), mx = warp_max(v);
             if (lane == 0) s_cqbox[d] = make_float2(mn, mx);
         }
+        __syncwarp();
+        for (int t = lane; t < G.n_tiles256; t += 32) {
+            float lb1 = 0.f, lb2 = 0.f;
+            for (int d = 0; d < dyz; ++d) {
+                const float2 b = G.tbox[(size_t)d * G.n_tiles256 + t];
+                const float2 q = s_cqbox[d];
+                const float l = fmaxf(fmaxf(__fsub_rn(b.x, q.y), __fsub_rn(q.x, b.y)), 0.f);
+                lb1 = fmaxf(lb1, l);
+                if (d >= dy) lb2 = fmaxf(lb2, l);
+            }
+            s_tlb[0][t] = lb1;
+            s_tlb[1][t] = lb2;
+        }
     }
     __syncthreads();
-    // Coarse test, taken identically by every thread without a barrier: it
-    // reads read-only data (tbox, s_cqbox) and `bound`, a register snapshot of
-    // the CTA's largest per-query bound taken right after a barrier.
-    const bool coarse = sorted && jt == 256 && G.tbox != nullptr;
     static_assert(LW * LQ == 32, "one bound per lane");
     auto snapshot = [&]() { return warp_max((&s_bound[0][0])[lane]); };
     auto tile_dead = [&](int t, bool pass1, float bound) {
-        if (!coarse) return false;
-        float lb = 0.f;
-#pragma unroll 4
-        for (int d = pass1 ? 0 : dy; d < dyz; ++d) {
-            const float2 b = G.tbox[(size_t)d * G.n_tiles256 + t];
-            const float2 q = s_cqbox[d];
-            lb = fmaxf(lb, fmaxf(fmaxf(__fsub_rn(b.x, q.y), __fsub_rn(q.x, b.y)), 0.f));
-        }
-        return lb >= bound;
+        return coarse && s_tlb[pass1 ? 0 : 1][t] >= bound;
     };
     const bool shared_perm = s_shared_perm != 0;
     const int32_t *perm0 = s_mperm[0];
@@ -921,31 +932,42 @@ __device__ __forceinline__ void ksg_lane_item(const KsgLaunch &L, const CUtensor
     // liveness of every (query, chunk) of the tile for this warp: bit 4c'+a of
     // word c/8; a lower bound (exact in float, rounding is monotone) on d_YZ
     // (pass 1) or d_Z (pass 2) below the query's bound keeps the chunk
+    // (The box loads of all of a tile's rounds of 8 chunks are issued
+    // together, dimension by dimension, so that a tile costs one chain of
+    // dependent loads per dimension rather than one per round.)
+    static_assert(256 / 64 == 4, "at most 4 rounds of 8 chunks per tile (jt <= 256)");
     auto tile_live = [&](int j0, int jn, bool pass1) {
         const int nct = (jn + 7) >> 3;
-        bool any = false;
-        for (int wb = 0; wb < wpt; ++wb) {
-            const int c = wb * 8 + (lane >> 2), a = lane & 3;
-            bool live = false;
-            if (c < nct) {
-                if (!sorted) {
-                    live = true;
-                } else {
-                    const float *qc = s_q + (warp * LQ + a) * dyz;
-                    const int gc = (j0 >> 3) + c;
-                    float lb = 0.f;
-#pragma unroll 4
-                    for (int d = pass1 ? 0 : dy; d < dyz; ++d) {
-                        const float2 b = __ldg(&G.box[(size_t)d * G.n_chunks8 + gc]);
-                        const float q = qc[d];
-                        lb = fmaxf(lb, fmaxf(fmaxf(__fsub_rn(b.x, q), __fsub_rn(q, b.y)), 0.f));
+        const int a = lane & 3;
+        float lb[4] = {0.f, 0.f, 0.f, 0.f};
+        if (sorted) {
+            const float *qc = s_q + (warp * LQ + a) * dyz;
+            const int gc0 = (j0 >> 3) + (lane >> 2), gmax = G.n_chunks8 - 1;
+#pragma unroll 2
+            for (int d = pass1 ? 0 : dy; d < dyz; ++d) {
+                const float q = qc[d];
+                const float2 *bd = G.box + (size_t)d * G.n_chunks8;
+#pragma unroll
+                for (int wb = 0; wb < 4; ++wb) {
+                    if (wb < wpt) {
+                        // past the group's last chunk: a valid address, result unused
+                        const float2 b = __ldg(&bd[min(gc0 + 8 * wb, gmax)]);
+                        lb[wb] = fmaxf(lb[wb],
+                                       fmaxf(fmaxf(__fsub_rn(b.x, q), __fsub_rn(q, b.y)), 0.f));
                     }
-                    live = lb < s_bound[warp][a];
                 }
             }
-            const unsigned word = __ballot_sync(0xffffffffu, live);
-            if (lane == 0) s_bits[warp * wpt + wb] = word;
-            any |= word != 0;
+        }
+        const float bnd = s_bound[warp][a];
+        bool any = false;
+#pragma unroll
+        for (int wb = 0; wb < 4; ++wb) {
+            if (wb < wpt) {
+                const bool live = wb * 8 + (lane >> 2) < nct && (!sorted || lb[wb] < bnd);
+                const unsigned word = __ballot_sync(0xffffffffu, live);
+                if (lane == 0) s_bits[warp * wpt + wb] = word;
+                any |= word != 0;
+            }
         }
         __syncwarp();
         return any;
