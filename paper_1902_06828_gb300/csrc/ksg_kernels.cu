@@ -696,6 +696,9 @@ __device__ __forceinline__ void ksg_lane_item(const KsgLaunch &L, const CUtensor
     // (pass 1 over (Y, Z), pass 2 over Z): tile t is skipped when it reaches
     // the CTA's largest bound
     __shared__ float s_tlb[2][kMaxOrderN / 256];
+    // pass 1 visits the tiles in increasing order of that bound (the home
+    // tile first), so that the thresholds fall early
+    __shared__ unsigned char s_tord[kMaxOrderN / 256];
     __shared__ __align__(8) unsigned long long s_tbar;   // tile-copy mbarrier (TMA)
     const uint32_t tbar = lane_smem_u32(&s_tbar);
     uint32_t tphase = 0;
@@ -789,6 +792,17 @@ __device__ __forceinline__ void ksg_lane_item(const KsgLaunch &L, const CUtensor
             }
             s_tlb[0][t] = lb1;
             s_tlb[1][t] = lb2;
+        }
+        __syncwarp();
+        const int home = min((qtile * LQC) / jt, G.n_tiles256 - 1);
+        for (int t = lane; t < G.n_tiles256; t += 32) {
+            const float kt = t == home ? -1.f : s_tlb[0][t];
+            int r = 0;
+            for (int u = 0; u < G.n_tiles256; ++u) {
+                const float ku = u == home ? -1.f : s_tlb[0][u];
+                r += ku < kt || (ku == kt && u < t);
+            }
+            s_tord[r] = (unsigned char)t;
         }
     }
     __syncthreads();
@@ -1043,13 +1057,18 @@ __device__ __forceinline__ void ksg_lane_item(const KsgLaunch &L, const CUtensor
         bool toggle = true;
         for (int s = 0; s < ntiles; ++s) {
             int t;
-            if (s == 0) t = home;
+            if (coarse) t = s_tord[s];
+            else if (s == 0) t = home;
             else if ((toggle && up < ntiles) || down < 0) t = up++;
             else t = down--;
             toggle = !toggle;
             const int j0 = t * jt;
             const int jn = min(jt, N - j0);
-            if (tile_dead(t, true, cbound)) continue;
+            // in bound order, every later tile is as far and the bound only falls
+            if (tile_dead(t, true, cbound)) {
+                if (coarse) break;
+                continue;
+            }
             const bool live = tile_live(j0, jn, true);
             const int buf_i = nchk++ & 1;
             if (lane == 0) s_live[buf_i][warp] = live;
