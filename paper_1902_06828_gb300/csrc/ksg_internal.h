@@ -24,7 +24,8 @@ struct GroupDesc {
     int n_mblocks;          // ceil(n_members / members per thread)
     long long item_begin;   // first CTA of the group in the launch
     // Spatial order (nullptr sigma = time order).  Points are processed in the
-    // leaf order of a k-d tree over the shared (Y, Z) coordinates: position p is
+    // leaf order of a k-d tree (large groups) or along a Morton curve over the
+    // shared (Y, Z) coordinates: position p is
     // time point sigma[p]; yz[d * N + p] holds Y (d < dy) and Z coordinates in
     // that order; box[d * n_chunks8 + c] = (min, max) of dim d over positions
     // 8c .. 8c + 7.  Only used with theiler == 0.
@@ -39,9 +40,9 @@ struct GroupDesc {
     const float *ysorted;
 };
 
-// One spatial-order job (one CTA): the k-d tree order of the (Y, Z) coordinates
-// of a group, built in shared memory; writes sigma, yz, box and tbox as
-// described above.
+// One spatial-order job (one CTA): the k-d tree or Morton order of the (Y, Z)
+// coordinates of a group, built in shared memory; writes sigma, yz, box and
+// tbox as described above.
 struct OrderJob {
     const float *base;
     int N, dyz;
@@ -50,8 +51,13 @@ struct OrderJob {
     float *yz;
     float2 *box;
     float2 *tbox;           // boxes of aligned 256-point tiles
+    int kd;                 // 1: k-d tree order, 0: Morton curve
 };
 constexpr int kMaxOrderN = 16384;   // points a CTA can sort in shared memory
+// groups of at least this many members take the k-d tree order: its build
+// (one sort per tree level, about 2 ms at N = 10^4) pays back in the kernel
+// only over many members; smaller groups take the one-sort Morton curve
+constexpr size_t kKdOrderMinMembers = 4096;
 cudaError_t launch_order(const OrderJob *jobs, int n_jobs, cudaStream_t st);
 
 struct ComposeJob {

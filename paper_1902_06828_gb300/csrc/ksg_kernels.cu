@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(QT) ksg_fused_kernel(const KsgLaunch L)
     const int jt = L.jt;
     const int cpt = jt >> 3;                  // chunks of 8 per tile
     const float *__restrict__ base = G.base;
-    const bool sorted = G.sigma != nullptr;   // k-d tree order over (Y, Z), theiler == 0
+    const bool sorted = G.sigma != nullptr;   // spatial order over (Y, Z), theiler == 0
 
     const int rows_t = dyz + M * dx;
     const int rows_q = dyz + (DX1 ? 0 : M * dx);
@@ -1592,16 +1592,21 @@ __global__ void fisher_yates_kernel(int32_t *out, long long stride, int n, uint6
             out[(long long)blockIdx.x * stride + i] = sperm[i];
 }
 
-// ---------------- spatial order: k-d tree over (Y, Z) ----------------
-// The points of a group are put in the leaf order of a k-d tree over the
-// (Y, Z) space.  A node of m > 8 points is split at the median of its widest
-// dimension into a first child of `kd_left(m)` points and a second child of
-// the rest; the first child's size is a multiple of 256 (nodes above 256
-// points) or of 8, so every node starts on a multiple of 8 (of 256 above 256
-// points), and every aligned 8-point chunk and 256-point tile is a union of
-// whole nodes: their bounding boxes, which the pruning tests, stay compact in
-// every dimension.  The order only affects how much work the pruning saves,
-// never a result.
+// ---------------- spatial order over (Y, Z) ----------------
+// The points of a group are processed in a spatial order of their shared
+// (Y, Z) coordinates, and every aligned chunk of 8 and tile of 256 ordered
+// points carries a bounding box that the pruning tests.  The order only
+// affects how much work the pruning saves, never a result.  Two orders:
+//  * a Morton curve (per-dimension ranges, keys of interleaved bits, one
+//    bitonic sort): cheap to build, for small launches;
+//  * the leaf order of a k-d tree: a node of m > 8 points is split at the
+//    median of its widest dimension into a first child of `kd_left(m)` points
+//    and a second child of the rest; the first child's size is a multiple of
+//    256 (nodes above 256 points) or of 8, so every node starts on a multiple
+//    of 8 (of 256 above 256 points) and every aligned chunk and tile is a union
+//    of whole nodes, whose boxes stay compact in every dimension.  It costs
+//    one sort per tree level and pays for large groups, where it cuts the
+//    chunks and tiles the pruning must visit.
 constexpr int kOrderMaxSeg = 2048;   // nodes that still split at one level (> 8 points: N / 9)
 constexpr size_t kOrderSmem = (size_t)kMaxOrderN * 8 + (size_t)kMaxOrderN * 2 +
                               6 * (size_t)kOrderMaxSeg * 4;
@@ -1626,17 +1631,97 @@ __device__ __forceinline__ int kd_left(int m)
     return left < blk ? blk : (left > m - 1 ? m - 1 : left);
 }
 
-// One CTA per group.  The tree is built level by level over the current
-// order: every node that still splits (the active nodes, start-ordered) finds
-// its widest dimension from per-dimension extents (segmented warp scans over
-// consecutive positions, then shared-memory atomics), and one bitonic sort of
-// the keys (node start, coordinate on that dimension, point) orders every
-// active node along its dimension at once; points of finished leaves key on
-// their own position and stay.  Then the sorted coordinates and the bounding
-// box of every aligned chunk of 8 and tile of 256 sorted points.
-__global__ void __launch_bounds__(1024) order_kernel(const OrderJob *jobs)
+
+// Ascending bitonic sort of P2 keys in shared memory (one CTA).
+__device__ void bitonic_sort_keys(unsigned long long *skeys, int P2)
 {
-    extern __shared__ unsigned long long skeys[];                 // [P2]
+    for (int kk = 2; kk <= P2; kk <<= 1) {
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int t = threadIdx.x; t < (P2 >> 1); t += blockDim.x) {
+                const int lo = 2 * jj * (t / jj) + (t % jj);
+                const int hi = lo + jj;
+                const bool up = (lo & kk) == 0;
+                const unsigned long long x = skeys[lo], y = skeys[hi];
+                if ((x > y) == up) {
+                    skeys[lo] = y;
+                    skeys[hi] = x;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Morton order: per-dimension ranges, keys of bits interleaved from the most
+// significant (up to 50 bits) packed with the point index, one sort.
+__device__ void morton_order(const OrderJob &J, unsigned long long *skeys, int P2)
+{
+    __shared__ float s_lo[32], s_hi[32];
+    __shared__ float s_red[2][32];
+    const int N = J.N, D = J.dyz;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nw = blockDim.x >> 5;
+    const float *base = J.base;
+    for (int d = 0; d < D; ++d) {
+        float mn = CUDART_INF_F, mx = -CUDART_INF_F;
+        for (int p = tid; p < N; p += blockDim.x) {
+            const float v = base[J.cols[d] + p];
+            mn = fminf(mn, v);
+            mx = fmaxf(mx, v);
+        }
+        mn = warp_min(mn);
+        mx = warp_max(mx);
+        if (lane == 0) {
+            s_red[0][wid] = mn;
+            s_red[1][wid] = mx;
+        }
+        __syncthreads();
+        if (wid == 0) {
+            mn = lane < nw ? s_red[0][lane] : CUDART_INF_F;
+            mx = lane < nw ? s_red[1][lane] : -CUDART_INF_F;
+            mn = warp_min(mn);
+            mx = warp_max(mx);
+            if (lane == 0) {
+                s_lo[d] = mn;
+                s_hi[d] = mx;
+            }
+        }
+        __syncthreads();
+    }
+    int bits = 50 / D;
+    if (bits > 24) bits = 24;
+    if (bits < 1) bits = 1;
+    const float qmax = (float)((1u << bits) - 1u);
+    for (int p = tid; p < P2; p += blockDim.x) {
+        unsigned long long key = ~0ull;
+        if (p < N) {
+            unsigned long long mort = 0;
+            unsigned int q[32];
+            for (int d = 0; d < D; ++d) {
+                const float span = s_hi[d] - s_lo[d];
+                float f = span > 0.f ? (base[J.cols[d] + p] - s_lo[d]) / span * qmax : 0.f;
+                f = fminf(fmaxf(f, 0.f), qmax);
+                q[d] = (unsigned int)f;
+            }
+            for (int b = bits - 1; b >= 0; --b)
+                for (int d = 0; d < D; ++d) mort = (mort << 1) | ((q[d] >> b) & 1u);
+            key = (mort << 14) | (unsigned long long)p;
+        }
+        skeys[p] = key;
+    }
+    __syncthreads();
+    bitonic_sort_keys(skeys, P2);
+}
+
+// k-d tree order, built level by level over the current order: every node
+// that still splits (the active nodes, start-ordered) finds its widest
+// dimension from per-dimension extents (segmented warp scans over consecutive
+// positions, then shared-memory atomics), and one bitonic sort of the keys
+// (node start, coordinate on that dimension, point) orders every active node
+// along its dimension at once; points of finished leaves key on their own
+// position and stay.
+__device__ void kd_order(const OrderJob &J, unsigned long long *skeys, int P2)
+{
     short *s_seg = reinterpret_cast<short *>(skeys + kMaxOrderN); // [N] active node of a position, -1 none
     int *s_start = reinterpret_cast<int *>(s_seg + kMaxOrderN);   // [kOrderMaxSeg] active nodes
     int *s_size = s_start + kOrderMaxSeg;
@@ -1645,12 +1730,9 @@ __global__ void __launch_bounds__(1024) order_kernel(const OrderJob *jobs)
     float *s_ext = reinterpret_cast<float *>(s_hi + kOrderMaxSeg);
     int *s_dim = reinterpret_cast<int *>(s_ext + kOrderMaxSeg);
     __shared__ int s_nact;
-    const OrderJob &J = jobs[blockIdx.x];
     const int N = J.N, D = J.dyz;
     const int tid = threadIdx.x, lane = tid & 31;
     const float *base = J.base;
-    int P2 = 1;
-    while (P2 < N) P2 <<= 1;
     for (int p = tid; p < P2; p += blockDim.x) skeys[p] = p < N ? (unsigned long long)p : ~0ull;
     if (tid == 0) {
         s_start[0] = 0;
@@ -1731,21 +1813,7 @@ __global__ void __launch_bounds__(1024) order_kernel(const OrderJob *jobs)
             skeys[p] = key;
         }
         __syncthreads();
-        for (int kk = 2; kk <= P2; kk <<= 1) {
-            for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-                for (int t = tid; t < (P2 >> 1); t += blockDim.x) {
-                    const int lo = 2 * jj * (t / jj) + (t % jj);
-                    const int hi = lo + jj;
-                    const bool up = (lo & kk) == 0;
-                    const unsigned long long x = skeys[lo], y = skeys[hi];
-                    if ((x > y) == up) {
-                        skeys[lo] = y;
-                        skeys[hi] = x;
-                    }
-                }
-                __syncthreads();
-            }
-        }
+        bitonic_sort_keys(skeys, P2);
         for (int p = tid; p < N; p += blockDim.x) skeys[p] &= 0x3FFFull;
         // the children that still split, in order (one warp; written to the
         // extent arrays, free now, then copied back)
@@ -1777,6 +1845,22 @@ __global__ void __launch_bounds__(1024) order_kernel(const OrderJob *jobs)
         }
         __syncthreads();
     }
+}
+
+// One CTA per group: the order (J.kd: k-d tree, else Morton curve), then the
+// sorted coordinates and the bounding box of every aligned chunk of 8 and
+// tile of 256 sorted points.
+__global__ void __launch_bounds__(1024) order_kernel(const OrderJob *jobs)
+{
+    extern __shared__ unsigned long long skeys[];
+    const OrderJob &J = jobs[blockIdx.x];
+    const int N = J.N, D = J.dyz;
+    const int tid = threadIdx.x;
+    const float *base = J.base;
+    int P2 = 1;
+    while (P2 < N) P2 <<= 1;
+    if (J.kd) kd_order(J, skeys, P2);
+    else morton_order(J, skeys, P2);
     for (int p = tid; p < N; p += blockDim.x) {
         const int t = (int)(skeys[p] & 0x3FFFull);
         J.sigma[p] = t;

@@ -605,6 +605,7 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
         J.yz = (float *)(obase + o.yz);
         J.box = (float2 *)(obase + o.box);
         J.tbox = (float2 *)(obase + o.tbox);
+        J.kd = g->members.size() >= kKdOrderMinMembers ? 1 : 0;
         ojobs.push_back(J);
     }
     std::vector<ComposeJob> cjobs;
