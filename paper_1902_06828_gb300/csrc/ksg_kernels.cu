@@ -1004,9 +1004,17 @@ __device__ __forceinline__ void ksg_lane_item(const KsgLaunch &L, const CUtensor
         if ((live4 >> a) & 1u) {
             const float *qc = s_q + (warp * LQ + a) * dyz;
             const float *tp = t_yz + c + u;
-#pragma unroll 4
-            for (int d = dy; d < dyz; ++d)
+            // two independent running maxima (max is exact in any order), so
+            // that the dimensions do not form one chain of dependent operations
+            float m1 = -CUDART_INF_F;
+            int d = dy;
+#pragma unroll 2
+            for (; d + 1 < dyz; d += 2) {
                 dzv = fmaxf(dzv, fabsf(__fsub_rn(qc[d], tp[d * jt])));
+                m1 = fmaxf(m1, fabsf(__fsub_rn(qc[d + 1], tp[(d + 1) * jt])));
+            }
+            if (d < dyz) dzv = fmaxf(dzv, fabsf(__fsub_rn(qc[d], tp[d * jt])));
+            dzv = fmaxf(dzv, m1);
             if (dy == 1) {
                 dyzv = fmaxf(dzv, fabsf(__fsub_rn(qc[0], tp[0])));
             } else {
@@ -1026,7 +1034,7 @@ __device__ __forceinline__ void ksg_lane_item(const KsgLaunch &L, const CUtensor
         // the ballot also orders these stores after every lane's reads of the
         // previous chunk's distances
         const unsigned kb = __ballot_sync(0xffffffffu, keep);
-        s_dz[(warp * LQ + a) * 8 + u] = dzv;
+        if (!pass1) s_dz[(warp * LQ + a) * 8 + u] = dzv;   // pass 1 reads d_YZ only
         s_dyz[(warp * LQ + a) * 8 + u] = dyzv;
         __syncwarp();
         return kb;
