@@ -907,11 +907,21 @@ __device__ __forceinline__ void ksg_lane_item(const KsgLaunch &L, const CUtensor
                         : "memory");
                 }
             }
-            // Y and Z of the whole tile, coalesced (jt <= blockDim)
+            // Y and Z of the whole tile, coalesced (jt <= blockDim); four
+            // dimensions' loads are issued before their stores, so that they
+            // are in flight together rather than one round trip each
             if (tid < jn)
-                for (int d = 0; d < dyz; ++d)
-                    t_yz[d * jt + tid] =
-                        sorted ? G.yz[(size_t)d * N + j0 + tid] : base[yz_off(d) + j0 + tid];
+                for (int d0 = 0; d0 < dyz; d0 += 4) {
+                    float v[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (d0 + e < dyz)
+                            v[e] = sorted ? G.yz[(size_t)(d0 + e) * N + j0 + tid]
+                                          : base[yz_off(d0 + e) + j0 + tid];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (d0 + e < dyz) t_yz[(d0 + e) * jt + tid] = v[e];
+                }
             const bool ok = tile_wait(tbar, tphase);
             tphase ^= 1u;
             if (__syncthreads_or(!ok)) {
