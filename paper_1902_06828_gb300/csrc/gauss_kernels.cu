@@ -147,60 +147,84 @@ __device__ bool chol_warp(double *a, int n, int ld)
     return true;
 }
 
-// ||L^-1||_F^2 for lower-triangular L (n <= kGaussMaxDims) by one warp: lane
-// c solves L x = e_c for c = lane and lane + 32 by forward substitution (x
-// kept in col[c][*], shared memory)
-__device__ double inv_frob2_warp(const double *L, int n, int ld,
-                                 double (*col)[kGaussMaxDims + 1])
+// Largest blocks the factor kernel holds: W = (Y, Z) has at most
+// kGaussMaxDims - 1 columns (X has at least one) and Z at most
+// kGaussMaxDims - 2 (Y has at least one).
+constexpr int kFacW = kGaussMaxDims - 1;
+constexpr int kFacZ = kGaussMaxDims - 2;
+constexpr int kFactorThreads = 128;
+
+// Column c's share of ||L^-1||_F^2 for lower-triangular L (n x n, row-major,
+// leading dimension ld): forward substitution of L x = e_c, the entries
+// x_c .. x_{n-1} kept in xs[0 .. n - c), summed in order of rows.
+__device__ double inv_col_sq(const double *L, int n, int ld, int c, double *xs)
 {
     double s = 0.0;
-    for (int c = threadIdx.x & 31; c < n; c += 32) {
-        for (int i = 0; i < n; ++i) {
-            double t = (i == c) ? 1.0 : 0.0;
-            for (int k = c; k < i; ++k) t -= L[i * ld + k] * col[c][k];
-            const double x = i < c ? 0.0 : t / L[i * ld + i];
-            col[c][i] = x;
-            s += x * x;
-        }
+    for (int i = c; i < n; ++i) {
+        double t = (i == c) ? 1.0 : 0.0;
+        for (int k = c; k < i; ++k) t -= L[i * ld + k] * xs[k - c];
+        const double x = t / L[i * ld + i];
+        xs[i - c] = x;
+        s += x * x;
     }
-    return warp_sum_d(s);
+    return s;
 }
 
-// Factor S_ZZ and S_WW (one warp).  W = the Y then Z columns; Z is the
-// trailing block of W.  Writes L_W, L_Z (lower, row-major, ld = dw) and
-// ||L^-1||_F^2 of each; status[0] = 1 if a block is not positive definite
-// (never cleared here, so estimates sharing a status word accumulate it).
+// Factor S_WW and S_ZZ (one CTA of kFactorThreads threads).  W = the Y then Z
+// columns; Z is the trailing block of W.  Warp 0 factors S_WW while warp 1
+// factors S_ZZ (GB300's FP64 pipe is narrow, so the two dependent chains run
+// on different schedulers); then every column of both inverses is solved by
+// a thread of its own (W's columns on threads 0-63, Z's on 64-127).  Writes
+// L_W, L_Z (lower, row-major, ld = dw) and ||L^-1||_F^2 of each; status[0] = 1
+// if a block is not positive definite (never cleared here, so estimates
+// sharing a status word accumulate it).
 __device__ __forceinline__ void gauss_factor_body(const GaussArgs &A)
 {
+    static_assert(kFacW <= 64 && kFacZ <= 64, "one thread per column, 64 per block");
     // the factorisations run in shared memory (a warp's dependent steps would
     // otherwise wait on global memory) and the factors are written back
-    __shared__ double col[kGaussMaxDims][kGaussMaxDims + 1];
-    __shared__ double sW[kGaussMaxDims * kGaussMaxDims], sZ[kGaussMaxDims * kGaussMaxDims];
-    if (threadIdx.x >= 32) return;
-    const int lane = threadIdx.x;
+    __shared__ double sW[kFacW * kFacW], sZ[kFacZ * kFacZ];
+    __shared__ double xW[kFacW * (kFacW + 1) / 2], xZ[kFacZ * (kFacZ + 1) / 2];
+    __shared__ double s_norm[kFactorThreads / 32];
+    __shared__ int s_ok[2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int dx = A.dx, dw = A.dw, dy = A.dy, dz = dw - dy, d = A.d;
-    for (int e = lane; e < dw * dw; e += 32) {
+    for (int e = tid; e < dw * dw; e += blockDim.x) {
         const int r = e / dw, c = e % dw;
-        sW[r * dw + c] = c <= r ? A.cov[(dx + r) * d + dx + c] : 0.0;
-        if (r < dz && c < dz) sZ[r * dw + c] = c <= r ? A.cov[(dx + dy + r) * d + dx + dy + c] : 0.0;
+        sW[e] = c <= r ? A.cov[(dx + r) * d + dx + c] : 0.0;
     }
-    __syncwarp();
-    bool ok = chol_warp(sW, dw, dw);
-    if (dz > 0) ok = ok && chol_warp(sZ, dz, dw);
-    if (lane == 0 && !ok) A.status[0] = 1;
-    if (!ok) return;
-    __syncwarp();
-    for (int e = lane; e < dw * dw; e += 32) {
-        const int r = e / dw, c = e % dw;
-        A.LW[e] = sW[e];
-        if (r < dz && c < dz) A.LZ[e] = sZ[e];
+    for (int e = tid; e < dz * dz; e += blockDim.x) {
+        const int r = e / dz, c = e % dz;
+        sZ[e] = c <= r ? A.cov[(dx + dy + r) * d + dx + dy + c] : 0.0;
     }
-    const double nw = inv_frob2_warp(sW, dw, dw, col);
-    __syncwarp();
-    const double nz = dz > 0 ? inv_frob2_warp(sZ, dz, dw, col) : 0.0;
-    if (lane == 0) {
-        A.norms[0] = nw;
-        A.norms[1] = nz;
+    __syncthreads();
+    if (warp == 0) {
+        const bool ok = chol_warp(sW, dw, dw);
+        if (lane == 0) s_ok[0] = ok;
+    } else if (warp == 1) {
+        const bool ok = dz > 0 ? chol_warp(sZ, dz, dz) : true;
+        if (lane == 0) s_ok[1] = ok;
+    }
+    __syncthreads();
+    if (!(s_ok[0] && s_ok[1])) {
+        if (tid == 0) A.status[0] = 1;
+        return;
+    }
+    for (int e = tid; e < dw * dw; e += blockDim.x) A.LW[e] = sW[e];
+    for (int e = tid; e < dz * dz; e += blockDim.x) A.LZ[(e / dz) * dw + e % dz] = sZ[e];
+    double s = 0.0;
+    if (tid < 64) {
+        if (tid < dw) s = inv_col_sq(sW, dw, dw, tid, xW + tid * dw - tid * (tid - 1) / 2);
+    } else {
+        const int c = tid - 64;
+        if (c < dz) s = inv_col_sq(sZ, dz, dz, c, xZ + c * dz - c * (c - 1) / 2);
+    }
+    s = warp_sum_d(s);
+    if (lane == 0) s_norm[warp] = s;
+    __syncthreads();
+    if (tid == 0) {
+        A.norms[0] = s_norm[0] + s_norm[1];
+        A.norms[1] = dz > 0 ? s_norm[2] + s_norm[3] : 0.0;
     }
 }
 
@@ -855,7 +879,7 @@ cudaError_t gauss_launch_batch_f64(const GaussArgs *args_dev, const GaussArgs *a
     }
     gauss_mean_batch<<<dim3(md, 1, n), 256, 0, st>>>(args_dev);
     gauss_cov_batch<<<dim3(md * (md + 1) / 2, 1, n), 256, 0, st>>>(args_dev);
-    gauss_factor_batch<<<dim3(1, 1, n), 32, 0, st>>>(args_dev);
+    gauss_factor_batch<<<dim3(1, 1, n), kFactorThreads, 0, st>>>(args_dev);
     gauss_centre_batch<<<dim3(8, mdx, n), 256, 0, st>>>(args_dev);
     gauss_cross_f64_batch<<<dim3(mrb, msp, n), kF64Rows, 0, st>>>(args_dev);
     gauss_cross_reduce_batch<<<dim3((unsigned)((mtot + 255) / 256), 1, n), 256, 0, st>>>(args_dev);
@@ -893,7 +917,7 @@ cudaError_t gauss_launch_stats(const GaussArgs &A, cudaStream_t st)
     gauss_cov_kernel<<<A.d * (A.d + 1) / 2, 256, 0, st>>>(A);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    gauss_factor_kernel<<<1, 32, 0, st>>>(A);
+    gauss_factor_kernel<<<1, kFactorThreads, 0, st>>>(A);
     return cudaGetLastError();
 }
 
