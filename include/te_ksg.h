@@ -359,12 +359,17 @@ te_status te_ctx_set_trace(te_ctx *ctx, te_trace_fn fn, void *user);
  *                                stream and launched as one graph; 0 (default):
  *                                direct launches.  The stream must not be
  *                                capturing already.
+ *   TE_OPT_KSG_ORDER             spatial order of the points the KSG kernels
+ *                                prune by: 1 = Morton curve, 2 = k-d tree;
+ *                                0 (default) = the k-d tree for groups of at
+ *                                least 4096 members, the Morton curve below
  * None of them changes a result.  Errors: TE_EINVAL for an unknown option or
  * value. */
 #define TE_OPT_KSG_TILE 1
 #define TE_OPT_KSG_MEMBERS_PER_LANE 2
 #define TE_OPT_PERSISTENT 3
 #define TE_OPT_GRAPH 4
+#define TE_OPT_KSG_ORDER 5
 te_status te_ctx_set_option(te_ctx *ctx, int32_t option, int64_t value);
 
 /* Counters of a context since its creation. */

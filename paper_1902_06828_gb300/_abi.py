@@ -78,7 +78,7 @@ class ServeStats(C.Structure):
 
 
 # te_ctx_set_option options (include/te_ksg.h)
-OPTIONS = {"ksg_tile": 1, "ksg_members_per_lane": 2, "persistent": 3, "graph": 4}
+OPTIONS = {"ksg_tile": 1, "ksg_members_per_lane": 2, "persistent": 3, "graph": 4, "ksg_order": 5}
 
 # every symbol include/te_ksg.h declares: name -> (restype, argtypes)
 _P = C.c_void_p

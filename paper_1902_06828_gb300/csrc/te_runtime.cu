@@ -605,7 +605,8 @@ te_status launch_groups(te_ctx *ctx, const std::vector<HostGroup> &groups, int n
         J.yz = (float *)(obase + o.yz);
         J.box = (float2 *)(obase + o.box);
         J.tbox = (float2 *)(obase + o.tbox);
-        J.kd = g->members.size() >= kKdOrderMinMembers ? 1 : 0;
+        J.kd = ctx->opt_order == 0 ? (g->members.size() >= kKdOrderMinMembers ? 1 : 0)
+                                   : (ctx->opt_order == 2 ? 1 : 0);
         ojobs.push_back(J);
     }
     std::vector<ComposeJob> cjobs;
@@ -823,6 +824,10 @@ te_status te_ctx_set_option(te_ctx *ctx, int32_t option, int64_t value)
     case TE_OPT_GRAPH:
         if (value != 0 && value != 1) return fail(ctx, TE_EINVAL, "the option takes 0 or 1");
         (option == TE_OPT_PERSISTENT ? ctx->opt_persistent : ctx->opt_graph) = (int)value;
+        return TE_OK;
+    case TE_OPT_KSG_ORDER:
+        if (value < 0 || value > 2) return fail(ctx, TE_EINVAL, "the order option takes 0, 1 or 2");
+        ctx->opt_order = (int)value;
         return TE_OK;
     default:
         return fail(ctx, TE_EINVAL, "unknown option");

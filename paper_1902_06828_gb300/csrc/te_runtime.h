@@ -90,7 +90,7 @@ struct te_ctx {
     void *trace_user = nullptr;
     // te_ctx_set_option: forced member-lane tile / members per lane (0 = the
     // tuning table), persistent member-lane grids, batches captured as graphs
-    int opt_jt = 0, opt_ms = 0, opt_persistent = 0, opt_graph = 0;
+    int opt_jt = 0, opt_ms = 0, opt_persistent = 0, opt_graph = 0, opt_order = 0;
 };
 
 namespace teksg {

@@ -1,7 +1,7 @@
 """Execution options (te_ctx_set_option) change how the work is launched,
-never a result: forced tile lengths and members per lane, persistent grids
-and batches captured as CUDA graphs give the same keys and the same network
-as the default (the tuning table)."""
+never a result: forced tile lengths and members per lane, persistent grids,
+batches captured as CUDA graphs and either spatial order of the points give
+the same keys and the same network as the default (the tuning table)."""
 import numpy as np
 import pytest
 
@@ -19,7 +19,7 @@ def env():
 
 
 def _reset(ctx):
-    for name in ("ksg_tile", "ksg_members_per_lane", "persistent", "graph"):
+    for name in ("ksg_tile", "ksg_members_per_lane", "persistent", "graph", "ksg_order"):
         ctx.set_option(name, 0)
 
 
@@ -43,6 +43,35 @@ def test_launch_shapes_and_forms_give_identical_keys(env):
             assert keys == ref, opts
     finally:
         _reset(ctx)
+
+
+@pytest.mark.parametrize("z", [[(0, 1)], [(0, 1), (4, 2), (7, 1)],
+                               [(0, 1), (0, 2), (1, 3), (2, 1), (5, 4), (8, 2), (9, 1)]])
+def test_morton_and_kd_orders_give_identical_keys(env, z):
+    """The Morton curve and the k-d tree order prune differently; every key of
+    every member agrees between them, and the unpermuted estimates agree with
+    the oracle (KSG estimator, Methods; conditioning sets of 1, 3 and 7
+    variables)."""
+    from oracle import ksg as oksg
+    te, ctx = env
+    s = np.asarray(synth.workload_var10(T=2000, seed=4)["series"], dtype=np.float32)
+    data = te.te_data_create(ctx, s)
+    cands = [(q, l) for q in (1, 3, 6) for l in (1, 2, 4) if (q, l) not in z][:7]
+    jobs = [te.Job(data, [c], [(0, 0)], z, k=4, max_lag=5, n_surr=40, seed=12,
+                   stream_tag=6) for c in cands]
+    got = {}
+    try:
+        for order in (1, 2):
+            _reset(ctx)
+            ctx.set_option("ksg_order", order)
+            _, got[order] = te.cmi_ksg_batch(ctx, jobs, return_keys=True)
+    finally:
+        _reset(ctx)
+    assert got[1] == got[2]
+    for c, keys in zip(cands, got[2]):
+        o = oksg.cmi_ksg(s, [c], [(0, 0)], z, k=4, max_lag=5)
+        assert keys[0] == o["key"], c
+    data.close()
 
 
 def test_network_with_graph_capture_and_persistent_grid(env):
