@@ -235,55 +235,63 @@ __device__ __forceinline__ void gauss_factor_body(const GaussArgs &A)
 // thread per surrogate keeps every FP64 lane busy (a warp per surrogate was
 // measured slower: GB300's FP64 pipe is narrow, so idle lanes cost more than
 // the dependent chain).
-__device__ __forceinline__ void gauss_schur_body(const GaussArgs &A, double gamma, int s)
+// One half of a surrogate's estimate: the Schur complement of X given Z
+// (which = 0, the trailing dz entries of W) or given W (which = 1) from the
+// factor L (lower, row-major, ld = dw), its log-determinant and the bound
+// on its error.
+__device__ __forceinline__ void gauss_schur_half(const GaussArgs &A, double gamma, int s,
+                                                 int which, const double *L, double &ld_out,
+                                                 double &bound_out)
 {
-    if (s > A.S) return;
     const int dx = A.dx, dw = A.dw, dy = A.dy, dz = dw - dy, d = A.d;
     const double *c = A.cross + (size_t)s * dx * dw;   // [dx][dw]
     double v[kGaussMaxDims], Sm[kGaussMaxX * kGaussMaxX], tmp[kGaussMaxDims];
-    double ld[2], bound[2];
     double sxx = 0.0;
     for (int a = 0; a < dx; ++a) sxx += A.cov[a * d + a];
-    for (int which = 0; which < 2; ++which) {
-        // which 0: given Z (trailing dz entries of W); 1: given W
-        const int n = which == 0 ? dz : dw;
-        const int off = which == 0 ? dy : 0;
-        const double *L = which == 0 ? A.LZ : A.LW;
-        // Sm = S_XX - V^T V, V = L^-1 C_V  (column per x dim)
-        for (int a = 0; a < dx; ++a)
-            for (int b = 0; b < dx; ++b) Sm[a * dx + b] = A.cov[a * d + b];
-        double vnorm2 = 0.0, svv = 0.0;
-        double vall[kGaussMaxX * kGaussMaxDims];
-        for (int r = 0; r < n; ++r) svv += A.covw[(dx + off + r) * d + dx + off + r];
-        for (int a = 0; a < dx; ++a) {
-            for (int r = 0; r < n; ++r) {
-                double t = c[a * dw + off + r];
-                for (int k = 0; k < r; ++k) t -= L[r * dw + k] * v[k];
-                v[r] = t / L[r * dw + r];
-                vnorm2 += v[r] * v[r];
-            }
-            for (int r = 0; r < n; ++r) vall[a * kGaussMaxDims + r] = v[r];
+    const int n = which == 0 ? dz : dw;
+    const int off = which == 0 ? dy : 0;
+    // Sm = S_XX - V^T V, V = L^-1 C_V  (column per x dim)
+    for (int a = 0; a < dx; ++a)
+        for (int b = 0; b < dx; ++b) Sm[a * dx + b] = A.cov[a * d + b];
+    double vnorm2 = 0.0, svv = 0.0;
+    double vall[kGaussMaxX * kGaussMaxDims];
+    for (int r = 0; r < n; ++r) svv += A.covw[(dx + off + r) * d + dx + off + r];
+    for (int a = 0; a < dx; ++a) {
+        for (int r = 0; r < n; ++r) {
+            double t = c[a * dw + off + r];
+            for (int k = 0; k < r; ++k) t -= L[r * dw + k] * v[k];
+            v[r] = t / L[r * dw + r];
+            vnorm2 += v[r] * v[r];
         }
-        const double dcnorm2 = gamma * gamma * sxx * svv;
-        for (int a = 0; a < dx; ++a)
-            for (int b = 0; b < dx; ++b) {
-                double t = 0.0;
-                for (int r = 0; r < n; ++r) t += vall[a * kGaussMaxDims + r] * vall[b * kGaussMaxDims + r];
-                Sm[a * dx + b] -= t;
-            }
-        if (!chol(Sm, dx, dx)) {
-            ld[which] = CUDART_NAN;
-            bound[which] = CUDART_INF;
-            continue;
-        }
-        double l = 0.0;
-        for (int a = 0; a < dx; ++a) l += 2.0 * log(Sm[a * dx + a]);
-        ld[which] = l;
-        // d ln|Sm| <= ||Sm^-1||_F ||dSm||_F,  ||dSm||_F <= 2 ||dC||_F ||L^-1||_F ||V||_F
-        const double sinv = sqrt(inv_frob2(Sm, dx, dx, tmp));
-        const double linv = n > 0 ? sqrt(A.norms[which == 0 ? 1 : 0]) : 0.0;
-        bound[which] = sinv * 2.0 * sqrt(dcnorm2) * linv * sqrt(vnorm2);
+        for (int r = 0; r < n; ++r) vall[a * kGaussMaxDims + r] = v[r];
     }
+    const double dcnorm2 = gamma * gamma * sxx * svv;
+    for (int a = 0; a < dx; ++a)
+        for (int b = 0; b < dx; ++b) {
+            double t = 0.0;
+            for (int r = 0; r < n; ++r) t += vall[a * kGaussMaxDims + r] * vall[b * kGaussMaxDims + r];
+            Sm[a * dx + b] -= t;
+        }
+    if (!chol(Sm, dx, dx)) {
+        ld_out = CUDART_NAN;
+        bound_out = CUDART_INF;
+        return;
+    }
+    double l = 0.0;
+    for (int a = 0; a < dx; ++a) l += 2.0 * log(Sm[a * dx + a]);
+    ld_out = l;
+    // d ln|Sm| <= ||Sm^-1||_F ||dSm||_F,  ||dSm||_F <= 2 ||dC||_F ||L^-1||_F ||V||_F
+    const double sinv = sqrt(inv_frob2(Sm, dx, dx, tmp));
+    const double linv = n > 0 ? sqrt(A.norms[which == 0 ? 1 : 0]) : 0.0;
+    bound_out = sinv * 2.0 * sqrt(dcnorm2) * linv * sqrt(vnorm2);
+}
+
+__device__ __forceinline__ void gauss_schur_body(const GaussArgs &A, double gamma, int s)
+{
+    if (s > A.S) return;
+    double ld[2], bound[2];
+    for (int which = 0; which < 2; ++which)
+        gauss_schur_half(A, gamma, s, which, which == 0 ? A.LZ : A.LW, ld[which], bound[which]);
     A.out[s] = 0.5 * (ld[0] - ld[1]);
     // factor 2 for second-order terms
     A.err[s] = 2.0 * 0.5 * (bound[0] + bound[1]);
@@ -792,9 +800,31 @@ __global__ void gauss_keys_kernel(const double *v, int n, long long *keys, int *
 __global__ void gauss_mean_kernel(GaussArgs A) { gauss_mean_body(A, blockIdx.x); }
 __global__ void gauss_cov_kernel(GaussArgs A) { gauss_cov_body(A, blockIdx.x); }
 __global__ void gauss_factor_kernel(GaussArgs A) { gauss_factor_body(A); }
-__global__ void gauss_schur_kernel(GaussArgs A, double gamma)
+// Single-call Schur step: the two halves of a surrogate run on a pair of
+// adjacent threads (the chains are independent and GB300's FP64 pipe is
+// narrow, so more threads in flight hide more of their latency), with both
+// factors read from shared memory; same arithmetic as gauss_schur_body.
+constexpr int kSchurThreads = 64;
+__global__ void __launch_bounds__(kSchurThreads) gauss_schur_kernel(GaussArgs A, double gamma)
 {
-    gauss_schur_body(A, gamma, blockIdx.x * blockDim.x + threadIdx.x);
+    __shared__ double sL[2][kFacW * kFacW];
+    const int dw = A.dw, dz = dw - A.dy;
+    for (int e = threadIdx.x; e < dw * dw; e += blockDim.x) {
+        sL[0][e] = (e / dw < dz && e % dw < dz) ? A.LZ[e] : 0.0;
+        sL[1][e] = A.LW[e];
+    }
+    __syncthreads();
+    const int s = blockIdx.x * (kSchurThreads / 2) + (int)(threadIdx.x >> 1);
+    const int which = threadIdx.x & 1;
+    double ld = 0.0, bound = 0.0;
+    if (s <= A.S) gauss_schur_half(A, gamma, s, which, sL[which], ld, bound);
+    const double ld_o = __shfl_xor_sync(0xffffffffu, ld, 1);
+    const double bound_o = __shfl_xor_sync(0xffffffffu, bound, 1);
+    if (s <= A.S && which == 0) {
+        A.out[s] = 0.5 * (ld - ld_o);
+        // factor 2 for second-order terms
+        A.err[s] = 2.0 * 0.5 * (bound + bound_o);
+    }
 }
 __global__ void gauss_cross_reduce_kernel(GaussArgs A)
 {
@@ -993,7 +1023,8 @@ double gauss_tc_gamma()
 
 cudaError_t gauss_launch_schur(const GaussArgs &A, double gamma, cudaStream_t st)
 {
-    gauss_schur_kernel<<<(A.S + 1 + 63) / 64, 64, 0, st>>>(A, gamma);
+    gauss_schur_kernel<<<(A.S + 1 + kSchurThreads / 2 - 1) / (kSchurThreads / 2), kSchurThreads, 0, st>>>(
+        A, gamma);
     return cudaGetLastError();
 }
 
