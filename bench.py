@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "KSG CMI estimates/s incl. surrogates at T=10000"
 UNIT = "estimates/s"
-TRAFFIC_PER_MEMBER_POINT = (146324736.0 + 4155392.0) / (9045 * 3995)
+TRAFFIC_PER_MEMBER_POINT = (146883584.0 + 4136448.0) / (9045 * 3995)
 
 
 def _peaks():
