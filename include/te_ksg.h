@@ -54,7 +54,7 @@ typedef struct {
     int32_t lag;  /* 0 = present, 1.. = past samples; lag <= the estimate's max lag */
 } te_var;
 
-/* Limits of this build. */
+/* Limits of the library. */
 #define TE_MAX_DIMS 32      /* dx + dy + dz of one KSG estimate */
 #define TE_GAUSS_MAX_DIMS 40 /* dx + dy + dz of one linear-Gaussian estimate (cmi_gauss,
                                 te_network_infer with estimator 1) */
