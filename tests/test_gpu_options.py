@@ -74,6 +74,33 @@ def test_morton_and_kd_orders_give_identical_keys(env, z):
     data.close()
 
 
+@pytest.mark.parametrize("T", [25, 16389])
+def test_orders_at_the_sorted_path_limits(env, T):
+    """The spatial orders at the smallest and largest group the sorted path
+    takes (N = 20 and N = 16384 points, where the k-d tree build fills its
+    shared-memory node list): identical keys, originals equal to the oracle."""
+    from oracle import ksg as oksg
+    te, ctx = env
+    s = np.asarray(synth.workload_var10(T=T, seed=6)["series"], dtype=np.float32)
+    data = te.te_data_create(ctx, s)
+    z = [(0, 1), (2, 1)]
+    cands = [(1, 1), (4, 2)]
+    jobs = [te.Job(data, [c], [(0, 0)], z, k=4, max_lag=5, n_surr=8, seed=3,
+                   stream_tag=2) for c in cands]
+    got = {}
+    try:
+        for order in (1, 2):
+            _reset(ctx)
+            ctx.set_option("ksg_order", order)
+            _, got[order] = te.cmi_ksg_batch(ctx, jobs, return_keys=True)
+    finally:
+        _reset(ctx)
+    assert got[1] == got[2]
+    for c, keys in zip(cands, got[2]):
+        assert keys[0] == oksg.cmi_ksg(s, [c], [(0, 0)], z, k=4, max_lag=5)["key"], c
+    data.close()
+
+
 def test_network_with_graph_capture_and_persistent_grid(env):
     te, ctx = env
     w = synth.workload_chain3(T=800, seed=3)
