@@ -55,6 +55,7 @@ int64_t g_keys_host[2 * (kStaticMaxSurr + 1)];
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 static_assert(sizeof(GroupDesc) <= 256, "the documented scratch size counts 256 bytes for it");
+static_assert(sizeof(MemberDesc) == 24, "the documented scratch size counts 24 bytes per member");
 
 te_status setup_device(int dev)
 {
